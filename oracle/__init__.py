@@ -1,0 +1,20 @@
+"""FP64 CPU oracle for the nuclear-structure DMRG hot path.
+
+TEST INFRASTRUCTURE.  Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import or run anything in this package.  The CUDA library and its
+Python binding never import it, and it imports nothing from them; the two share only the
+seeded input generator ``gen``.
+
+Contents and pins (each checked by a ``-m "not gpu"`` test):
+* ``hamiltonian``: Eq. (1) in the m-scheme determinant basis, dense exact
+  diagonalization.  Pinned by the two-particle spectra (they equal the J-coupled matrix
+  elements plus single-particle energies), the seniority closed form of a single-j
+  pairing Hamiltonian, J-multiplet containment across 2M sectors, the one-body closed
+  form, Hermiticity, and the dimension integers quoted for the pf shell.
+* ``mpo``: the normal / complementary operator partition of H at every bond.  Pinned by
+  brute force: sum_k L_k R_k rebuilt on the full Fock space of small chains equals H from
+  Jordan-Wigner matrices, at every bond, in both operator modes.
+* ``dmrg``: two-site DMRG.  Pinned by full-M runs reproducing exact diagonalization,
+  the variational bound, energies non-increasing in M, Hermiticity of H_eff,
+  H_eff on exact states, and truncation error -> 0 at full M.
+"""

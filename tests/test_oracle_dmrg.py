@@ -1,0 +1,132 @@
+"""Pins of the oracle two-site DMRG."""
+import numpy as np
+import pytest
+
+from gen import make_problem, initial_mps
+from oracle.hamiltonian import ChainHamiltonian, ed_lowest, fock_matrix
+from oracle.dmrg import OracleDMRG, enlarge_left, enlarge_right
+
+
+@pytest.fixture(scope="module")
+def ptoy():
+    p = make_problem("p", 2, 2, 0, seed=12)
+    return p, ed_lowest(p)[0]
+
+
+def test_full_m_reproduces_exact(ptoy):
+    """Large enough M converges to the full CI energy (two-site DMRG, full M)."""
+    p, e0 = ptoy
+    d = OracleDMRG(p, initial_mps(p, 6, 5))
+    res = d.sweep(10 ** 6)
+    assert abs(res[-1].energy - e0) < 1e-10
+    assert max(r.trunc_err for r in res) < 1e-13
+    res = d.sweep(10 ** 6)
+    # with complete bases the predicted wave function is already the eigenvector
+    assert all(r.n_products == 1 for r in res)
+    assert all(abs(r.energy - e0) < 1e-10 for r in res)
+
+
+def test_full_m_sd_shell():
+    p = make_problem("sd", 2, 2, 0, seed=1)
+    e0 = ed_lowest(p)[0]
+    d = OracleDMRG(p, initial_mps(p, 8, 5))
+    res = d.sweep(400)       # >= every bond's full compatible dimension
+    assert abs(res[-1].energy - e0) < 1e-10
+
+
+def test_variational_and_monotone_in_m(ptoy):
+    p, e0 = ptoy
+    d = OracleDMRG(p, initial_mps(p, 3, 7))
+    last = None
+    for M in (3, 6, 12):
+        for _ in range(2):
+            res = d.sweep(M)
+        es = [r.energy for r in res]
+        assert min(es) >= e0 - 1e-10
+        if last is not None:
+            assert res[-1].energy <= last + 1e-9
+        last = res[-1].energy
+
+
+def _basis_vectors(d, p):
+    """Explicit Fock-space vectors of the enlarged left and right spaces at position p."""
+    ch = d.ch
+    Lv = {}
+    e = enlarge_left(d.left[-1] if False else None, 0, d.mpo, ch) if False else None
+    # left blocks 0..p-1
+    vec = {(0, 0, 0): np.ones((1, 1))}
+    for b in range(0, p):
+        blk_prev = None if b == 0 else d.left[b - 1]
+        from oracle.dmrg import vacuum
+        enl = enlarge_left(vacuum(1, 0) if b == 0 else d.left[b - 1], b, d.mpo, ch)
+        ev = {}
+        for Q in enl.sectors:
+            cols = []
+            for (sg, q, off, dd) in enl.pieces[Q]:
+                e_s = np.eye(2)[:, sg]
+                for i in range(dd):
+                    cols.append(np.kron(vec[q][:, i], e_s))
+            ev[Q] = np.stack(cols, axis=1)
+        vec = {Q: ev[Q] @ d.UL[b][Q] for Q in d.UL[b]}
+    Lenl = enlarge_left(d.left[p - 1], p, d.mpo, ch)
+    Lv = {}
+    for Q in Lenl.sectors:
+        cols = []
+        for (sg, q, off, dd) in Lenl.pieces[Q]:
+            for i in range(dd):
+                cols.append(np.kron(vec[q][:, i], np.eye(2)[:, sg]))
+        Lv[Q] = np.stack(cols, axis=1)
+    N = ch.N
+    rvec = {(0, 0, 0): np.ones((1, 1))}
+    from oracle.dmrg import vacuum
+    for b in range(N - 2, p, -1):
+        enl = enlarge_right(vacuum(1, 0) if b == N - 2 else d.right[b + 1], b + 1, d.mpo, ch)
+        ev = {}
+        for Q in enl.sectors:
+            cols = []
+            for (sg, q, off, dd) in enl.pieces[Q]:
+                for i in range(dd):
+                    cols.append(np.kron(np.eye(2)[:, sg], rvec[q][:, i]))
+            ev[Q] = np.stack(cols, axis=1)
+        rvec = {Q: ev[Q] @ d.UR[b][Q] for Q in d.UR[b]}
+    Renl = enlarge_right(d.right[p + 1], p + 1, d.mpo, ch)
+    Rv = {}
+    for Q in Renl.sectors:
+        cols = []
+        for (sg, q, off, dd) in Renl.pieces[Q]:
+            for i in range(dd):
+                cols.append(np.kron(np.eye(2)[:, sg], rvec[q][:, i]))
+        Rv[Q] = np.stack(cols, axis=1)
+    return Lv, Rv
+
+
+@pytest.mark.parametrize("p_at", [2, 5, 8])
+def test_heff_equals_projected_hamiltonian(p_at):
+    """At truncated M, H_eff from renormalized block operators equals P^T H P with P the
+    explicit superblock basis in the full Fock space (pins enlargement, Jordan-Wigner
+    signs, renormalization and the wave-function layout)."""
+    p = make_problem("p", 2, 2, 0, seed=12)
+    d = OracleDMRG(p, initial_mps(p, 5, 5))
+    d.sweep(5)
+    for q in range(1, p_at):
+        d.run_step(q, "L", 5)
+    sb = d.superblock(p_at)
+    Lv, Rv = _basis_vectors(d, p_at)
+    cols = []
+    for (QL, QR, dL, dR, off) in sb.layout.blocks:
+        for i in range(dL):
+            for j in range(dR):
+                cols.append(np.kron(Lv[QL][:, i], Rv[QR][:, j]))
+    P = np.stack(cols, axis=1)
+    assert np.allclose(P.T @ P, np.eye(P.shape[1]), atol=1e-12)
+    H = fock_matrix(d.ch)
+    Hp = P.T @ (H @ P)
+    n = sb.layout.size
+    He = np.stack([sb.apply(np.eye(n)[:, c]) for c in range(n)], axis=1)
+    assert np.max(np.abs(He - Hp)) < 1e-11
+    # Hermitian, and Davidson reaches the lowest eigenvalue of the dense H_eff
+    assert np.max(np.abs(He - He.T)) < 1e-12
+    from oracle.dmrg import davidson
+    th, x, _, _ = davidson(sb.apply, sb.diagonal(), np.ones(n), tol=1e-10)
+    assert abs(th - np.linalg.eigvalsh(He)[0]) < 1e-10
+    assert np.allclose(sb.diagonal(), np.diag(He), atol=1e-12)
