@@ -1,0 +1,172 @@
+/*
+ * libdmrg -- C-ABI of the GB300 two-site DMRG hot path for nuclear shell-model
+ * Hamiltonians (Legeza, Veis, Poves, Dukelsky, "Advanced density matrix renormalization
+ * group method for nuclear structure calculations").
+ *
+ * Conventions common to every entry point
+ * ---------------------------------------
+ * - Every function returns an int status: DMRG_OK (0) or a negative DMRG_E* code.  No
+ *   exception and no abort crosses the ABI; dmrg_last_error() returns a description of
+ *   the last failure of a context (a pointer owned by the context, valid until the next
+ *   call on it).
+ * - Host arrays passed in are owned by the caller and copied before the call returns.
+ * - Device buffers allocated by the library belong to the context and are released by
+ *   dmrg_destroy().  Arguments documented as "device" are CUDA device pointers owned by
+ *   the caller; they must hold the stated number of float64 elements.
+ * - All work is issued on the stream given in dmrg_options.stream (NULL: the legacy
+ *   default stream).  Calls that return numbers to the host synchronise that stream.
+ * - Sectors are q = (N_p, N_n, 2M_z) integer triples in lexicographic order.  Chain
+ *   position c holds site order[c]; bond b lies between positions b and b+1.
+ * - A two-site step at position p (1 <= p <= N-3) treats the superblock
+ *   (left block, positions 0..p-1) (x) site p (x) site p+1 (x) (right block, p+2..N-1)
+ *   (two-site variant, "Xi_l (x) Lambda_{i+1} (x) Lambda_{i+2} (x) Xi_r").
+ *   The wave function is block-sparse: one dense row-major block per enlarged-left sector
+ *   Q_L whose partner q_T - Q_L exists on the enlarged right, blocks in Q_L order.
+ */
+#ifndef LIBDMRG_DMRG_H
+#define LIBDMRG_DMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DMRG_OK 0
+#define DMRG_EINVAL (-1)    /* bad argument, inconsistent input, or call out of order */
+#define DMRG_ENOMEM (-2)    /* device or host allocation failed                       */
+#define DMRG_ECUDA (-3)     /* a CUDA call failed (message has the CUDA error string)  */
+#define DMRG_ENOCONV (-4)   /* Davidson hit dav_max_iter before the tolerance          */
+#define DMRG_ETIMEOUT (-5)  /* a device-side wait gave up (bounded spin)               */
+
+#define DMRG_FP64 0         /* every contraction in FP64                               */
+#define DMRG_MIXED_FP32 1   /* operator contractions in FP32, Davidson/eig/energy FP64 */
+
+typedef struct dmrg_ctx dmrg_ctx;
+
+/* The shell-model Hamiltonian of Eq. (1) on m-scheme orbitals alpha = (n,l,j,m,tau_z):
+ *   H = sum_i eps_i n_i + sum_{i<j, k<l} vbar[ij,kl] c+_i c+_j c_l c_k
+ * (antisymmetrised two-body matrix elements; the list must contain both (ij,kl) and
+ * (kl,ij) and every entry must conserve N_p, N_n and 2M).  Indices are site indices. */
+typedef struct {
+  int32_t n_sites;          /* N, 4 <= N <= 64                                        */
+  const int8_t* species;    /* [N] 0 = proton, 1 = neutron                             */
+  const int8_t* two_m;      /* [N] 2 m of the orbital                                  */
+  const double* eps;        /* [N] single-particle energies (MeV)                      */
+  int64_t n_v;              /* number of two-body entries                              */
+  const int32_t* v_idx;     /* [4 n_v] (i, j, k, l) with i < j and k < l               */
+  const double* v_val;      /* [n_v] vbar (MeV)                                        */
+  const int32_t* order;     /* [N] chain position -> site (a permutation)              */
+  int32_t Np, Nn, two_Mz;   /* target sector ("m-scheme for J_z = 0": two_Mz = 0)      */
+} dmrg_problem;
+
+typedef struct {
+  int32_t precision;        /* DMRG_FP64 or DMRG_MIXED_FP32                            */
+  int32_t reserved0;
+  double dav_tol;           /* Davidson residual-norm tolerance (MeV), e.g. 1e-8       */
+  int32_t dav_max_iter;     /* maximum H_eff products per step, e.g. 100               */
+  int32_t dav_max_sub;      /* subspace size before thick restart, 4..64, e.g. 24      */
+  void* stream;             /* cudaStream_t, NULL = default stream                     */
+} dmrg_options;
+
+/* Starting state: right-block bases for bonds b = N-3 down to 2.  The right block of
+ * bond b is a truncation of (site b+1) (x) (right block of bond b+1); an enlarged sector
+ * lists its rows piece by piece, site state 0 (block sector Q) then site state 1 (block
+ * sector Q - q_site), each piece in block-state order.  For every kept sector: (N_p,
+ * N_n, 2M, D, m) with D the enlarged dimension (must match) and a D x m row-major matrix
+ * with orthonormal columns.  Replaces the paper's CI-DEAS warm-up. */
+typedef struct {
+  int32_t n_bonds;
+  const int32_t* bonds;     /* [n_bonds] N-3, N-4, ..., 2                              */
+  const int32_t* bond_ptr;  /* [n_bonds + 1] sector ranges                             */
+  const int32_t* sec;       /* [5 n_sec] Np, Nn, 2M, D, m                              */
+  const int64_t* u_off;     /* [n_sec + 1] element offsets into u                      */
+  const double* u;          /* isometries                                              */
+} dmrg_mps_init;
+
+typedef struct {
+  int32_t n_products;       /* H_eff applications                                      */
+  int32_t converged;        /* 1 if residual <= dav_tol                                */
+  double residual;          /* |H x - theta x|                                         */
+  double energy;            /* Ritz value (MeV); FP64 Rayleigh quotient in mixed mode  */
+  double heff_flops;        /* algorithmic flops of one H_eff product                  */
+  double heff_bytes;        /* algorithmic bytes of one H_eff product                  */
+  double seconds;           /* wall time of the call                                   */
+} dmrg_dav_stats;
+
+typedef struct {
+  int32_t p, dir;           /* position and direction (0 = left to right, 1 = back)    */
+  int32_t n_products, kept;
+  double energy, residual, trunc_err, seconds;
+} dmrg_step_stats;
+
+/* Create a context for one problem (Eq. 1 and a target state).  Validates the input
+ * (permutation, index ranges, i<j and k<l, quantum-number conservation, Hermitian list)
+ * and builds the normal / complementary operator partition on the host.  Status:
+ * DMRG_EINVAL on invalid input, DMRG_ENOMEM. */
+int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dmrg_ctx** out);
+
+/* Release every host and device resource of the context.  NULL is accepted. */
+int dmrg_destroy(dmrg_ctx* ctx);
+
+/* Description of the last error of the context (never NULL). */
+const char* dmrg_last_error(const dmrg_ctx* ctx);
+
+/* Build the block operators: the left block of bond 0 (site 0), the right block of bond
+ * N-2 (site N-1), and the right blocks of bonds N-3..2 by renormalizing with the given
+ * starting state (sweeping "from right to left" once).  Must precede every call below.
+ * DMRG_EINVAL if the starting state does not match the sector structure. */
+int dmrg_build_blocks(dmrg_ctx* ctx, const dmrg_mps_init* init);
+
+/* Wave-function layout at position p.  Pass NULL arrays to query n_blocks and size;
+ * then arrays of n_blocks entries: qn_left [3 n_blocks], dl, dr, off. */
+int dmrg_psi_layout(dmrg_ctx* ctx, int32_t p, int64_t* n_blocks, int64_t* size,
+                    int32_t* qn_left, int32_t* dl, int32_t* dr, int64_t* off);
+
+/* psi_out = H_eff psi_in at position p with the current blocks (device pointers, size
+ * from dmrg_psi_layout; in-place is not allowed).  The superblock Hamiltonian is
+ * sum_k (L_k P^{|R_k|}) (x) R_k over the operator products of bond p (Section on the
+ * two-site superblock).  Contractions in the context's precision. */
+int dmrg_heff_apply(dmrg_ctx* ctx, int32_t p, const double* psi_in_dev, double* psi_out_dev);
+
+/* Lowest eigenpair of H_eff at position p by Davidson's method (the variational
+ * minimisation of the energy).  guess_dev: device vector (NULL = the context's
+ * prediction from the previous step, or the uniform vector at the first step).
+ * psi_out_dev: optional device copy of the normalised Ritz vector.  The eigenvector is
+ * kept in the context for dmrg_truncate_renormalize.  DMRG_ENOCONV if the tolerance
+ * was not reached within dav_max_iter products (energy and vector are still returned). */
+int dmrg_davidson(dmrg_ctx* ctx, int32_t p, const double* guess_dev, double* psi_out_dev,
+                  double* energy, dmrg_dav_stats* stats);
+
+/* Truncation and renormalization after the Davidson step at position p (SVD theorem
+ * basis change): dir 0 keeps M states of the enlarged left block (left block of bond p),
+ * dir 1 of the enlarged right block (right block of bond p); reduced density matrix per
+ * sector, FP64 eigendecomposition on the device, global selection of the M largest
+ * weights (extended to the whole degenerate multiplet at the cut), and renormalization of
+ * every normal and complementary operator of the new block.  trunc_err = discarded
+ * weight; kept = number of kept states.  DMRG_EINVAL if no eigenvector is held for p. */
+int dmrg_truncate_renormalize(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t M,
+                              double* trunc_err, int32_t* kept);
+
+/* One two-site step: H_eff at p, Davidson from the predicted guess, truncation and
+ * renormalization in direction dir. */
+int dmrg_step(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t M, dmrg_step_stats* st);
+
+/* One sweep = positions 1..N-3 left to right then N-3..1 back ("sweeping back and
+ * forth").  steps: optional array of 2(N-3) records.  energy: energy of the last step. */
+int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy);
+
+/* Sectors and dimensions of a stored block basis: side 0 = left block of bond b,
+ * side 1 = right block of bond b.  NULL arrays query n. */
+int dmrg_block_sectors(dmrg_ctx* ctx, int32_t side, int32_t b, int32_t* n, int32_t* qn,
+                       int32_t* dims);
+
+/* Algorithmic cost of one H_eff product at position p: flops (2 per multiply-add, the
+ * cheaper order of the two products of each term) and bytes (operator blocks read once
+ * plus wave function in and out, at the element size of the context's precision). */
+int dmrg_heff_cost(dmrg_ctx* ctx, int32_t p, double* flops, double* bytes, int64_t* n_items);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

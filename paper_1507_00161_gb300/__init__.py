@@ -1,0 +1,240 @@
+"""Python binding of libdmrg, the GB300 two-site DMRG hot path (C-ABI in include/dmrg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.  Device
+vectors are passed as torch CUDA tensors (float64, contiguous) or raw device pointers.
+Importing this package does not need a GPU; creating a context does.  The library must
+have been built (``paper_1507_00161_gb300.build.build()``); there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdmrg.so")
+
+DMRG_OK = 0
+DMRG_EINVAL = -1
+DMRG_ENOMEM = -2
+DMRG_ECUDA = -3
+DMRG_ENOCONV = -4
+DMRG_ETIMEOUT = -5
+FP64 = 0
+MIXED_FP32 = 1
+
+EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
+            "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
+            "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
+            "dmrg_heff_cost"]
+
+
+class DmrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdmrg status {code}: {msg}")
+        self.code = code
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int32), ("species", ctypes.c_void_p),
+                ("two_m", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("n_v", ctypes.c_int64),
+                ("v_idx", ctypes.c_void_p), ("v_val", ctypes.c_void_p),
+                ("order", ctypes.c_void_p), ("Np", ctypes.c_int32), ("Nn", ctypes.c_int32),
+                ("two_Mz", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("dav_tol", ctypes.c_double), ("dav_max_iter", ctypes.c_int32),
+                ("dav_max_sub", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class MpsInit(ctypes.Structure):
+    _fields_ = [("n_bonds", ctypes.c_int32), ("bonds", ctypes.c_void_p),
+                ("bond_ptr", ctypes.c_void_p), ("sec", ctypes.c_void_p),
+                ("u_off", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+
+
+class DavStats(ctypes.Structure):
+    _fields_ = [("n_products", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("residual", ctypes.c_double), ("energy", ctypes.c_double),
+                ("heff_flops", ctypes.c_double), ("heff_bytes", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("dir", ctypes.c_int32), ("n_products", ctypes.c_int32),
+                ("kept", ctypes.c_int32), ("energy", ctypes.c_double),
+                ("residual", ctypes.c_double), ("trunc_err", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdmrg.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdmrg is not built ({path} missing); run "
+                          "paper_1507_00161_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "dmrg_create": [ctypes.POINTER(Problem), ctypes.POINTER(Options), ctypes.POINTER(P)],
+        "dmrg_destroy": [P],
+        "dmrg_build_blocks": [P, ctypes.POINTER(MpsInit)],
+        "dmrg_psi_layout": [P, i32, P, P, P, P, P, P],
+        "dmrg_heff_apply": [P, i32, P, P],
+        "dmrg_davidson": [P, i32, P, P, P, ctypes.POINTER(DavStats)],
+        "dmrg_truncate_renormalize": [P, i32, i32, i32, P, P],
+        "dmrg_step": [P, i32, i32, i32, ctypes.POINTER(StepStats)],
+        "dmrg_sweep": [P, i32, P, P],
+        "dmrg_block_sectors": [P, i32, i32, P, P, P],
+        "dmrg_heff_cost": [P, i32, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.dmrg_last_error.argtypes = [P]
+    lib.dmrg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, or an int pointer, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None and a.size else None
+
+
+class DMRG:
+    """One problem (Eq. 1 on m-scheme sites, a target sector) on the GPU."""
+
+    def __init__(self, problem, precision=FP64, dav_tol=1e-8, dav_max_iter=100, dav_max_sub=24,
+                 stream=None):
+        self.lib = load_library()
+        self._keep = dict(
+            species=np.ascontiguousarray(problem.species, dtype=np.int8),
+            two_m=np.ascontiguousarray(problem.two_m, dtype=np.int8),
+            eps=np.ascontiguousarray(problem.eps, dtype=np.float64),
+            v_idx=np.ascontiguousarray(problem.v_idx, dtype=np.int32).reshape(-1),
+            v_val=np.ascontiguousarray(problem.v_val, dtype=np.float64),
+            order=np.ascontiguousarray(problem.order, dtype=np.int32))
+        k = self._keep
+        self.n_sites = int(k["species"].shape[0])
+        pr = Problem(self.n_sites, k["species"].ctypes.data, k["two_m"].ctypes.data,
+                     k["eps"].ctypes.data, int(k["v_val"].shape[0]),
+                     k["v_idx"].ctypes.data if k["v_idx"].size else None,
+                     k["v_val"].ctypes.data if k["v_val"].size else None,
+                     k["order"].ctypes.data, int(problem.Np), int(problem.Nn),
+                     int(problem.two_Mz))
+        stream_ptr = None
+        if stream is not None:
+            stream_ptr = stream if isinstance(stream, int) else stream.cuda_stream
+        opt = Options(int(precision), 0, float(dav_tol), int(dav_max_iter), int(dav_max_sub),
+                      stream_ptr)
+        h = ctypes.c_void_p()
+        rc = self.lib.dmrg_create(ctypes.byref(pr), ctypes.byref(opt), ctypes.byref(h))
+        self.h = h.value
+        if rc != DMRG_OK:
+            msg = self.lib.dmrg_last_error(self.h).decode() if self.h else "create failed"
+            self.close()
+            raise DmrgError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmrg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != DMRG_OK and rc not in allow:
+            raise DmrgError(rc, self.lib.dmrg_last_error(self.h).decode())
+        return rc
+
+    def build_blocks(self, init):
+        bonds, bond_ptr, sec, u_off, u = init.flat() if hasattr(init, "flat") else init
+        self._init_keep = [np.ascontiguousarray(a) for a in (bonds, bond_ptr, sec, u_off, u)]
+        b, bp, s, uo, uu = self._init_keep
+        mi = MpsInit(int(b.shape[0]), _np_ptr(b), _np_ptr(bp), _np_ptr(s), _np_ptr(uo),
+                     _np_ptr(uu))
+        self._check(self.lib.dmrg_build_blocks(self.h, ctypes.byref(mi)))
+
+    def psi_layout(self, p):
+        n = ctypes.c_int64()
+        size = ctypes.c_int64()
+        self._check(self.lib.dmrg_psi_layout(self.h, p, ctypes.byref(n), ctypes.byref(size),
+                                             None, None, None, None))
+        nb = n.value
+        qn = np.zeros((nb, 3), dtype=np.int32)
+        dl = np.zeros(nb, dtype=np.int32)
+        dr = np.zeros(nb, dtype=np.int32)
+        off = np.zeros(nb, dtype=np.int64)
+        self._check(self.lib.dmrg_psi_layout(self.h, p, None, None, _np_ptr(qn), _np_ptr(dl),
+                                             _np_ptr(dr), _np_ptr(off)))
+        return dict(qn_left=qn, dl=dl, dr=dr, off=off, size=size.value)
+
+    def heff_apply(self, p, x, y):
+        self._check(self.lib.dmrg_heff_apply(self.h, p, _ptr(x), _ptr(y)))
+
+    def davidson(self, p, guess=None, out=None, allow_noconv=False):
+        e = ctypes.c_double()
+        st = DavStats()
+        rc = self.lib.dmrg_davidson(self.h, p, _ptr(guess), _ptr(out), ctypes.byref(e),
+                                    ctypes.byref(st))
+        self._check(rc, allow=(DMRG_ENOCONV,) if allow_noconv else ())
+        return e.value, {f: getattr(st, f) for f, _ in DavStats._fields_}
+
+    def truncate_renormalize(self, p, direction, M):
+        tr = ctypes.c_double()
+        kept = ctypes.c_int32()
+        self._check(self.lib.dmrg_truncate_renormalize(self.h, p, direction, M, ctypes.byref(tr),
+                                                       ctypes.byref(kept)))
+        return tr.value, kept.value
+
+    def step(self, p, direction, M):
+        st = StepStats()
+        self._check(self.lib.dmrg_step(self.h, p, direction, M, ctypes.byref(st)))
+        return st.as_dict()
+
+    def sweep(self, M):
+        n = 2 * (self.n_sites - 3)
+        arr = (StepStats * n)()
+        e = ctypes.c_double()
+        self._check(self.lib.dmrg_sweep(self.h, M, arr, ctypes.byref(e)))
+        return [a.as_dict() for a in arr], e.value
+
+    def block_sectors(self, side, b):
+        n = ctypes.c_int32()
+        self._check(self.lib.dmrg_block_sectors(self.h, side, b, ctypes.byref(n), None, None))
+        qn = np.zeros((n.value, 3), dtype=np.int32)
+        d = np.zeros(n.value, dtype=np.int32)
+        self._check(self.lib.dmrg_block_sectors(self.h, side, b, None, _np_ptr(qn), _np_ptr(d)))
+        return qn, d
+
+    def heff_cost(self, p):
+        f = ctypes.c_double()
+        b = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.dmrg_heff_cost(self.h, p, ctypes.byref(f), ctypes.byref(b),
+                                            ctypes.byref(n)))
+        return f.value, b.value, n.value

@@ -1,0 +1,267 @@
+// Internal definitions shared by the translation units of libdmrg (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg.h"
+
+namespace dmrg {
+
+// ---------------------------------------------------------------------------------------
+// errors: every failure inside the library throws Error; the C-ABI turns it into a status
+// ---------------------------------------------------------------------------------------
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define DMRG_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::dmrg::Error(DMRG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define DMRG_REQUIRE(cond, code, msg)                 \
+  do {                                                \
+    if (!(cond)) throw ::dmrg::Error((code), (msg)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// quantum numbers q = (N_p, N_n, 2M)
+// ---------------------------------------------------------------------------------------
+struct QN {
+  int32_t a, b, m;
+};
+inline bool operator<(const QN& x, const QN& y) {
+  if (x.a != y.a) return x.a < y.a;
+  if (x.b != y.b) return x.b < y.b;
+  return x.m < y.m;
+}
+inline bool operator==(const QN& x, const QN& y) { return x.a == y.a && x.b == y.b && x.m == y.m; }
+inline bool operator!=(const QN& x, const QN& y) { return !(x == y); }
+inline QN operator+(const QN& x, const QN& y) { return {x.a + y.a, x.b + y.b, x.m + y.m}; }
+inline QN operator-(const QN& x, const QN& y) { return {x.a - y.a, x.b - y.b, x.m - y.m}; }
+inline int particles(const QN& q) { return q.a + q.b; }
+
+// sorted sector list with dimensions
+struct SectorSet {
+  std::vector<QN> q;
+  std::vector<int> d;
+  int find(const QN& x) const {
+    auto it = std::lower_bound(q.begin(), q.end(), x);
+    if (it == q.end() || *it != x) return -1;
+    return int(it - q.begin());
+  }
+  int size() const { return int(q.size()); }
+  int64_t total() const {
+    int64_t t = 0;
+    for (int x : d) t += x;
+    return t;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------------------
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  int64_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(int64_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count > 0) {
+      cudaError_t e = cudaMalloc(&p, sizeof(T) * size_t(count));
+      if (e != cudaSuccess) {
+        p = nullptr;
+        throw Error(DMRG_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed");
+      }
+      n = count;
+    }
+  }
+  void upload(const T* h, int64_t count, cudaStream_t s) {
+    alloc(count);
+    if (count) DMRG_CUDA(cudaMemcpyAsync(p, h, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+  }
+  void upload(const std::vector<T>& h, cudaStream_t s) { upload(h.data(), int64_t(h.size()), s); }
+};
+
+// ---------------------------------------------------------------------------------------
+// generic grouped GEMM task lists:  C (M x N) += sum_terms alpha op(A) op(B)
+// operands are (base index, element offset, leading dimension) so that one list serves
+// any set of base pointers (wave-function vectors change between Davidson products)
+// ---------------------------------------------------------------------------------------
+enum Base : int32_t {
+  B_LOPS = 0,   // enlarged left operators
+  B_ROPS = 1,   // enlarged right operators
+  B_X = 2,      // input vector / matrix
+  B_Y = 3,      // output
+  B_T = 4,      // scratch
+  B_U = 5,      // isometries
+  B_V = 6,      // isometries (second set)
+  B_Z = 7,      // extra
+  NBASE = 8
+};
+
+struct Operand {
+  int64_t off;
+  int32_t base;
+  int32_t ld;
+};
+struct GemmTerm {
+  Operand A, B;
+  int32_t K;
+  int32_t trans;   // bit0: A transposed (A stored K x M), bit1: B transposed (B stored N x K)
+  double alpha;
+};
+struct GemmTask {
+  Operand C;
+  int32_t M, N;
+  int32_t t0, t1;   // terms [t0, t1)
+};
+// tile of a large task for the shared-memory kernel
+struct GemmTile {
+  int32_t task;
+  int32_t m0, n0;
+};
+
+template <class T>
+struct Bases {
+  T* p[NBASE];
+};
+
+// host-side task list builder
+struct TaskList {
+  std::vector<GemmTask> tasks;
+  std::vector<GemmTerm> terms;
+  void begin_task(Operand C, int M, int N) {
+    GemmTask t;
+    t.C = C;
+    t.M = M;
+    t.N = N;
+    t.t0 = int(terms.size());
+    t.t1 = t.t0;
+    tasks.push_back(t);
+  }
+  void add_term(Operand A, Operand B, int K, int trans, double alpha) {
+    GemmTerm g;
+    g.A = A;
+    g.B = B;
+    g.K = K;
+    g.trans = trans;
+    g.alpha = alpha;
+    terms.push_back(g);
+    tasks.back().t1 = int(terms.size());
+  }
+  void clear() { tasks.clear(); terms.clear(); }
+};
+
+// device-resident, split into small (warp per task) and large (tiled) parts
+struct DevTaskList {
+  DevBuf<GemmTask> small_tasks, large_tasks;
+  DevBuf<GemmTerm> terms;
+  DevBuf<GemmTile> tiles;
+  int64_t n_small = 0, n_large = 0, n_tiles = 0;
+  double flops = 0;      // algorithmic flops of the list
+  // base_elems[b]: elements addressable through base b (0 = unused); every operand range
+  // is checked against it on the host before the list reaches the device
+  void build(const TaskList& L, const int64_t* base_elems, cudaStream_t s);
+};
+
+
+// copy-scale tasks: dst (rows x cols, ld_dst) += sum_terms scale * src (rows x cols, ld_src)
+struct CopyTerm {
+  Operand src;
+  double scale;
+};
+struct CopyTask {
+  Operand dst;
+  int32_t rows, cols;
+  int32_t t0, t1;
+};
+struct CopyList {
+  std::vector<CopyTask> tasks;
+  std::vector<CopyTerm> terms;
+};
+void validate_copy_tasks(const CopyList& L, const int64_t* base_elems);
+
+// ---------------------------------------------------------------------------------------
+// kernels (kernels.cu)
+// ---------------------------------------------------------------------------------------
+template <class T>
+void run_gemm_tasks(const DevTaskList& L, const Bases<T>& b, int beta_zero, cudaStream_t s);
+template <class T>
+void run_copy_tasks(const CopyTask* d_tasks, int64_t n_tasks, const CopyTerm* d_terms,
+                    const Bases<T>& b, cudaStream_t s);
+
+// Davidson / vector kernels
+void multidot(const double* const* d_vecs, int k, const double* w, int64_t n, double* d_out,
+              double* d_partials, cudaStream_t s);
+// out = beta out + coef_scale sum_j coef[j] vecs[j]
+void lincomb(const double* const* d_vecs, const double* d_coef, int k, int64_t n, double* out,
+             double beta_out, double coef_scale, cudaStream_t s);
+// d_out[0] = a . b (fixed reduction order)
+void dot(const double* a, const double* b, int64_t n, double* d_out, double* d_partials,
+         cudaStream_t s);
+void davidson_residual(const double* x, const double* Ax, const double* d_theta, int64_t n,
+                       double* r, cudaStream_t s);
+void davidson_correction(const double* r, const double* diag, const double* d_theta, int64_t n,
+                         double* t, cudaStream_t s);
+void scale_vec(double* x, int64_t n, const double* d_scale, int invert_sqrt, cudaStream_t s);
+void fill_value(double* x, int64_t n, double v, cudaStream_t s);
+
+// diagonal of H_eff: for each psi element the sum over diagonal-preserving terms
+struct DiagTask {
+  int64_t psi_off;
+  int32_t dL, dR;
+  int32_t t0, t1;
+};
+struct DiagTerm {
+  int64_t loff, roff;   // diagonal blocks in the enlarged left / right operator arenas
+  int32_t ldl, ldr;
+};
+void heff_diag(const DiagTask* d_tasks, int n_tasks, const DiagTerm* d_terms,
+               const double* lops, const double* rops, double* out, cudaStream_t s);
+
+// batched symmetric eigensolver (parallel cyclic Jacobi, FP64), one block per matrix:
+// A at off[s] (n x n, destroyed), V scratch (n x n), Vs sorted sign-fixed eigenvectors,
+// w at woff[s] (eigenvalues, descending or ascending, optionally clipped at 0)
+void batched_eigh2(const int64_t* d_off, const int64_t* d_woff, const int32_t* d_dim, int n,
+                   double* d_A, double* d_V, double* d_Vs, double* d_w, int descending, int clip,
+                   cudaStream_t s);
+void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w, double* d_Y,
+                cudaStream_t s);
+// global selection: k-th largest of w[0..n) (ties irrelevant for the value), result in out[0]
+void kth_largest(const double* w, int64_t n, int64_t k, double* d_scratch, double* out,
+                 cudaStream_t s);
+// kept[s] = number of w >= max(lambda_M (1 - 1e-10), 1e-14) in sector s (w descending)
+void count_kept(const int64_t* d_woff, const int32_t* d_dim, int nsec, const double* w,
+                const double* d_lamM, int32_t* d_kept, double* d_kept_weight, cudaStream_t s);
+void gather_u(const int64_t* d_voff, const int32_t* d_dim, const int32_t* d_kept,
+              const int64_t* d_uoff, int nsec, const double* Vs, double* U, cudaStream_t s);
+void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+void to_f64(const float* x, double* y, int64_t n, cudaStream_t s);
+
+}  // namespace dmrg

@@ -1,0 +1,1322 @@
+// libdmrg: two-site DMRG on the GPU for the shell-model Hamiltonian of Eq. (1).
+//
+// Host code here does the integer bookkeeping (sectors, block lists, task lists); every
+// floating-point step runs in the kernels of kernels.cu:
+//   enlargement of block operators by one site (copy tasks), H_eff psi (two task-list
+//   GEMM stages per product), Davidson vector algebra and the Ritz problem, reduced
+//   density matrices, their eigendecomposition, selection of the kept states,
+//   renormalization of every normal and complementary operator, and the prediction of
+//   the next wave function.
+#include <chrono>
+#include <cmath>
+#include <memory>
+#include <set>
+
+#include "common.h"
+#include "problem.h"
+
+namespace dmrg {
+
+// ---------------------------------------------------------------------------------------
+// block-sparse operator sets and enlarged layouts
+// ---------------------------------------------------------------------------------------
+struct OpBlock {
+  int32_t so, si;
+  int64_t off;
+};
+
+struct OpSet {
+  SectorSet sec;
+  int nlab = 0;
+  std::vector<int64_t> lab_ptr;   // [nlab + 1]
+  std::vector<OpBlock> blocks;
+  DevBuf<double> data;
+  DevBuf<float> data32;
+  int64_t n_elems = 0;
+  std::vector<int32_t> by_in;     // nlab x nsec: block index by input sector (or -1)
+  void index_by_in() {
+    by_in.assign(size_t(nlab) * sec.size(), -1);
+    for (int k = 0; k < nlab; ++k)
+      for (int64_t x = lab_ptr[k]; x < lab_ptr[k + 1]; ++x)
+        by_in[size_t(k) * sec.size() + blocks[x].si] = int32_t(x);
+  }
+};
+
+// enlarged space: block (x) site (left) or site (x) block (right); piece sigma = 0 first
+struct Layout {
+  SectorSet sec;
+  std::vector<std::array<int, 2>> pblk;   // block sector of piece sigma (or -1)
+  std::vector<std::array<int, 2>> poff;   // row offset of piece sigma
+};
+
+// basis of a stored block: kept columns of an isometry per enlarged sector
+struct Iso {
+  Layout lay;
+  std::vector<int> m;            // kept states per enlarged sector
+  std::vector<int64_t> uoff;     // offset of U (D x m, row-major) per enlarged sector
+  std::vector<int> kept_idx;     // enlarged sector -> stored sector index (or -1)
+  std::vector<int> enl_idx;      // stored sector -> enlarged sector
+  DevBuf<double> data;
+  bool identity = false;         // every state kept unrotated (no truncation)
+};
+
+struct Blk {
+  OpSet ops;
+  Iso iso;
+  bool valid = false;
+};
+
+struct Super {
+  int p = -1;
+  Layout Ll, Rl;
+  OpSet L, R;
+  std::vector<int> bL, bR, bdl, bdr;   // psi blocks: sector indices and dims
+  std::vector<int64_t> boff;
+  std::vector<int> psi_of_L, psi_of_R;
+  int64_t size = 0;
+  DevTaskList st1, st2;
+  int64_t t_elems = 0;
+  double flops = 0, bytes = 0;
+  int64_t n_items = 0;
+  DevBuf<DiagTask> dtasks;
+  DevBuf<DiagTerm> dterms;
+  int n_dtasks = 0;
+  DevBuf<double> diag;
+  bool diag_ready = false;
+};
+
+}  // namespace dmrg
+
+struct dmrg_ctx {
+  std::string err = "no error";
+  dmrg::Chain chain;
+  dmrg::MPO mpo;
+  dmrg_options opt{};
+  cudaStream_t stream = nullptr;
+  int N = 0;
+  std::vector<std::set<std::tuple<int, int, int>>> reach_left, reach_right;
+  std::vector<dmrg::Blk> left, right;
+  bool built = false;
+  std::unique_ptr<dmrg::Super> sb;
+  // Davidson workspace
+  dmrg::DevBuf<double> V, AV, r, t, x, Ax, x1, Ax1, small, partials;
+  dmrg::DevBuf<const double*> vptr;
+  int64_t ws_n = 0, ws_sub = 0;
+  // current eigenvector and what the next guess needs
+  dmrg::DevBuf<double> psi, psi_guess;
+  bool psi_valid = false;
+  int psi_p = -1;
+  std::unique_ptr<dmrg::Super> prev;   // layouts of the superblock psi belongs to
+  // scratch
+  dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
+  dmrg::DevBuf<float> f32a, f32b, f32T;
+  // precomputed per-site W entry orders (grouped by destination label)
+  std::vector<std::vector<int>> w_by_b, w_by_a;
+};
+
+namespace dmrg {
+
+using Ctx = dmrg_ctx;
+
+static bool reachable(const std::set<std::tuple<int, int, int>>& s, const QN& q) {
+  return s.count(std::make_tuple(q.a, q.b, q.m)) > 0;
+}
+
+static void build_reach(Ctx& c) {
+  const int N = c.N;
+  c.reach_left.assign(N + 1, {});
+  c.reach_right.assign(N + 1, {});
+  c.reach_left[0].insert({0, 0, 0});
+  for (int x = 0; x < N; ++x) {
+    auto s = c.reach_left[x];
+    for (auto& t : c.reach_left[x]) {
+      QN q{std::get<0>(t), std::get<1>(t), std::get<2>(t)};
+      QN r = q + c.chain.q[x];
+      s.insert({r.a, r.b, r.m});
+    }
+    c.reach_left[x + 1] = s;
+  }
+  c.reach_right[N].insert({0, 0, 0});
+  for (int x = N - 1; x >= 0; --x) {
+    auto s = c.reach_right[x + 1];
+    for (auto& t : c.reach_right[x + 1]) {
+      QN q{std::get<0>(t), std::get<1>(t), std::get<2>(t)};
+      QN r = q + c.chain.q[x];
+      s.insert({r.a, r.b, r.m});
+    }
+    c.reach_right[x] = s;
+  }
+}
+
+static const int kOpEntries[4][2][2] = {
+    // {n_entries, ...} encoded as pairs (sigma_out, sigma_in); -1 = unused
+    {{0, 0}, {1, 1}},     // I
+    {{1, 1}, {-1, -1}},   // N
+    {{1, 0}, {-1, -1}},   // C+
+    {{0, 1}, {-1, -1}},   // C
+};
+
+// enlarged layout of blk with site s; left: positions 0..s (complement s+1..N-1)
+static void make_layout(const Ctx& c, const SectorSet& blk, int s, bool left, Layout& lay) {
+  const QN qs = c.chain.q[s];
+  std::vector<QN> cand;
+  for (auto& q : blk.q) {
+    cand.push_back(q);
+    cand.push_back(q + qs);
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  lay.sec.q.clear();
+  lay.sec.d.clear();
+  lay.pblk.clear();
+  lay.poff.clear();
+  const QN T = c.chain.target;
+  for (auto& Q : cand) {
+    bool ok = left ? reachable(c.reach_right[s + 1], T - Q) : reachable(c.reach_left[s], T - Q);
+    if (!ok) continue;
+    int b0 = blk.find(Q), b1 = blk.find(Q - qs);
+    int d0 = b0 >= 0 ? blk.d[b0] : 0, d1 = b1 >= 0 ? blk.d[b1] : 0;
+    if (d0 + d1 == 0) continue;
+    lay.sec.q.push_back(Q);
+    lay.sec.d.push_back(d0 + d1);
+    lay.pblk.push_back({b0, b1});
+    lay.poff.push_back({0, d0});
+  }
+}
+
+// operators of the enlarged space (see problem.cu for the recursion); the Jordan-Wigner
+// sign is (-1)^{|op| N(q_in)} on the left and (-1)^{sigma_in |O_block|} on the right
+static void enlarge(Ctx& c, const OpSet& blk, int s, bool left, Layout& lay, OpSet& out) {
+  make_layout(c, blk.sec, s, left, lay);
+  const int nE = lay.sec.size();
+  const QN qs = c.chain.q[s];
+  // block sector -> enlarged sector for sigma = 0, 1
+  std::vector<int> e0(blk.sec.size(), -1), e1(blk.sec.size(), -1);
+  for (int i = 0; i < blk.sec.size(); ++i) {
+    e0[i] = lay.sec.find(blk.sec.q[i]);
+    e1[i] = lay.sec.find(blk.sec.q[i] + qs);
+  }
+  const auto& W = c.mpo.W[s];
+  const auto& order = left ? c.w_by_b[s] : c.w_by_a[s];
+  const int nlab_out = left ? int(c.mpo.labels[s + 1].size()) : int(c.mpo.labels[s].size());
+  const auto& src_par = left ? c.mpo.parity[s] : c.mpo.parity[s + 1];
+  out.sec = lay.sec;
+  out.nlab = nlab_out;
+  out.lab_ptr.assign(nlab_out + 1, 0);
+  out.blocks.clear();
+  std::vector<int32_t> blk_of(size_t(nlab_out) * nE, -1);
+  std::vector<std::array<int32_t, 4>> task_of;   // per out block: task per (so, si)
+  std::vector<int32_t> tcount;
+  std::vector<CopyTask> tasks;
+  // pass 1: blocks, tasks, term counts
+  auto visit = [&](auto&& fn) {
+    for (int ei : order) {
+      const WEntry& e = W[ei];
+      const int srcl = left ? e.a : e.b, dstl = left ? e.b : e.a;
+      for (int x = 0; x < 2; ++x) {
+        const int so = kOpEntries[e.op][x][0], si = kOpEntries[e.op][x][1];
+        if (so < 0) continue;
+        for (int64_t bi = blk.lab_ptr[srcl]; bi < blk.lab_ptr[srcl + 1]; ++bi) {
+          const OpBlock& ob = blk.blocks[bi];
+          const int Qi = si ? e1[ob.si] : e0[ob.si];
+          const int Qo = so ? e1[ob.so] : e0[ob.so];
+          if (Qi < 0 || Qo < 0) continue;
+          double sign = 1.0;
+          if (left) {
+            if ((e.op == OP_CD || e.op == OP_C) && (particles(blk.sec.q[ob.si]) & 1)) sign = -1.0;
+          } else {
+            if (si && src_par[srcl]) sign = -1.0;
+          }
+          fn(dstl, Qo, Qi, so, si, ob, e.coef * sign);
+        }
+      }
+    }
+  };
+  int cur_label = -1;
+  visit([&](int dstl, int Qo, int Qi, int so, int si, const OpBlock& ob, double) {
+    (void)ob;
+    if (dstl != cur_label) {
+      DMRG_REQUIRE(dstl > cur_label, DMRG_EINVAL, "internal: entries not grouped by label");
+      for (int l = cur_label + 1; l <= dstl; ++l) out.lab_ptr[l] = int64_t(out.blocks.size());
+      cur_label = dstl;
+    }
+    int32_t& bid = blk_of[size_t(dstl) * nE + Qi];
+    if (bid < 0) {
+      bid = int32_t(out.blocks.size());
+      out.blocks.push_back(OpBlock{Qo, Qi, 0});
+      task_of.push_back({-1, -1, -1, -1});
+    }
+    int32_t& tid = task_of[bid][so * 2 + si];
+    if (tid < 0) {
+      tid = int32_t(tasks.size());
+      CopyTask t;
+      t.dst.base = B_Y;
+      t.dst.off = bid;   // fixed up below
+      t.dst.ld = 0;
+      t.rows = blk.sec.d[lay.pblk[Qo][so]];
+      t.cols = blk.sec.d[lay.pblk[Qi][si]];
+      t.t0 = so * 2 + si;   // piece code, fixed up below
+      t.t1 = 0;
+      tasks.push_back(t);
+      tcount.push_back(0);
+    }
+    tcount[tid]++;
+  });
+  for (int l = cur_label + 1; l <= nlab_out; ++l) out.lab_ptr[l] = int64_t(out.blocks.size());
+  int64_t off = 0;
+  for (auto& b : out.blocks) {
+    b.off = off;
+    off += int64_t(lay.sec.d[b.so]) * lay.sec.d[b.si];
+  }
+  out.n_elems = off;
+  std::vector<int32_t> tpos(tasks.size());
+  int32_t acc = 0;
+  for (size_t t = 0; t < tasks.size(); ++t) {
+    const OpBlock& b = out.blocks[tasks[t].dst.off];
+    const int so = tasks[t].t0 >> 1, si = tasks[t].t0 & 1;
+    const int Di = lay.sec.d[b.si];
+    tasks[t].dst.off = b.off + int64_t(lay.poff[b.so][so]) * Di + lay.poff[b.si][si];
+    tasks[t].dst.ld = Di;
+    tasks[t].t0 = acc;
+    tpos[t] = acc;
+    acc += tcount[t];
+    tasks[t].t1 = acc;
+  }
+  std::vector<CopyTerm> terms(acc);
+  visit([&](int dstl, int Qo, int Qi, int so, int si, const OpBlock& ob, double scale) {
+    (void)Qo;
+    int32_t bid = blk_of[size_t(dstl) * nE + Qi];
+    int32_t tid = task_of[bid][so * 2 + si];
+    CopyTerm& g = terms[tpos[tid]++];
+    g.src.base = B_X;
+    g.src.off = ob.off;
+    g.src.ld = blk.sec.d[ob.si];
+    g.scale = scale;
+  });
+  out.data.alloc(std::max<int64_t>(out.n_elems, 1));
+  {
+    CopyList chk;
+    chk.tasks = tasks;
+    chk.terms = terms;
+    int64_t be[NBASE] = {0};
+    be[B_X] = blk.data.n;
+    be[B_Y] = out.data.n;
+    validate_copy_tasks(chk, be);
+  }
+  DMRG_CUDA(cudaMemsetAsync(out.data.p, 0, sizeof(double) * std::max<int64_t>(out.n_elems, 1),
+                            c.stream));
+  DevBuf<CopyTask> dt;
+  DevBuf<CopyTerm> dg;
+  dt.upload(tasks, c.stream);
+  dg.upload(terms, c.stream);
+  Bases<double> bb{};
+  bb.p[B_X] = blk.data.p;
+  bb.p[B_Y] = out.data.p;
+  run_copy_tasks<double>(dt.p, int64_t(tasks.size()), dg.p, bb, c.stream);
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));   // task buffers are freed on return
+  out.index_by_in();
+}
+
+// stored block = kept part of an enlarged operator set: O' = U_o^T O U_i per block
+static void project(Ctx& c, OpSet& E, const Iso& iso, OpSet& out) {
+  if (iso.identity) {
+    out = std::move(E);
+    out.index_by_in();
+    return;
+  }
+  const int nE = E.sec.size();
+  out.sec.q.clear();
+  out.sec.d.clear();
+  for (int i = 0; i < nE; ++i)
+    if (iso.m[i] > 0) {
+      out.sec.q.push_back(E.sec.q[i]);
+      out.sec.d.push_back(iso.m[i]);
+    }
+  out.nlab = E.nlab;
+  out.lab_ptr.assign(E.nlab + 1, 0);
+  out.blocks.clear();
+  TaskList A, B;
+  int64_t toff = 0, noff = 0;
+  for (int k = 0; k < E.nlab; ++k) {
+    out.lab_ptr[k] = int64_t(out.blocks.size());
+    for (int64_t x = E.lab_ptr[k]; x < E.lab_ptr[k + 1]; ++x) {
+      const OpBlock& b = E.blocks[x];
+      const int no = iso.kept_idx[b.so], ni = iso.kept_idx[b.si];
+      if (no < 0 || ni < 0) continue;
+      const int Do = E.sec.d[b.so], Di = E.sec.d[b.si], mo = iso.m[b.so], mi = iso.m[b.si];
+      A.begin_task(Operand{toff, B_T, mi}, Do, mi);
+      A.add_term(Operand{b.off, B_X, Di}, Operand{iso.uoff[b.si], B_U, mi}, Di, 0, 1.0);
+      B.begin_task(Operand{noff, B_Y, mi}, mo, mi);
+      B.add_term(Operand{iso.uoff[b.so], B_U, mo}, Operand{toff, B_T, mi}, Do, 1, 1.0);
+      out.blocks.push_back(OpBlock{no, ni, noff});
+      toff += int64_t(Do) * mi;
+      noff += int64_t(mo) * mi;
+    }
+  }
+  out.lab_ptr[E.nlab] = int64_t(out.blocks.size());
+  out.n_elems = noff;
+  out.data.alloc(std::max<int64_t>(noff, 1));
+  c.tmp.alloc(std::max<int64_t>(toff, 1));
+  DevTaskList dA, dB;
+  int64_t be[NBASE] = {0};
+  be[B_X] = E.data.n;
+  be[B_T] = c.tmp.n;
+  be[B_U] = iso.data.n;
+  be[B_Y] = out.data.n;
+  dA.build(A, be, c.stream);
+  dB.build(B, be, c.stream);
+  Bases<double> bb{};
+  bb.p[B_X] = E.data.p;
+  bb.p[B_T] = c.tmp.p;
+  bb.p[B_U] = iso.data.p;
+  bb.p[B_Y] = out.data.p;
+  run_gemm_tasks<double>(dA, bb, 1, c.stream);
+  run_gemm_tasks<double>(dB, bb, 1, c.stream);
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  out.index_by_in();
+}
+
+static void identity_iso(Ctx& c, const Layout& lay, Iso& iso) {
+  iso.lay = lay;
+  const int n = lay.sec.size();
+  iso.m = lay.sec.d;
+  iso.uoff.assign(n, 0);
+  iso.kept_idx.resize(n);
+  iso.enl_idx.resize(n);
+  std::vector<double> h;
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    iso.kept_idx[i] = i;
+    iso.enl_idx[i] = i;
+    iso.uoff[i] = off;
+    off += int64_t(lay.sec.d[i]) * lay.sec.d[i];
+  }
+  h.assign(off, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int r = 0; r < lay.sec.d[i]; ++r) h[iso.uoff[i] + int64_t(r) * lay.sec.d[i] + r] = 1.0;
+  iso.data.upload(h, c.stream);
+  iso.identity = true;
+}
+
+static void finish_iso_index(Iso& iso) {
+  const int n = iso.lay.sec.size();
+  iso.kept_idx.assign(n, -1);
+  iso.enl_idx.clear();
+  for (int i = 0; i < n; ++i)
+    if (iso.m[i] > 0) {
+      iso.kept_idx[i] = int(iso.enl_idx.size());
+      iso.enl_idx.push_back(i);
+    }
+}
+
+static OpSet vacuum_ops(int nlab, int which, cudaStream_t s) {
+  OpSet v;
+  v.sec.q = {QN{0, 0, 0}};
+  v.sec.d = {1};
+  v.nlab = nlab;
+  v.lab_ptr.assign(nlab + 1, 0);
+  for (int k = which + 1; k <= nlab; ++k) v.lab_ptr[k] = 1;
+  v.blocks = {OpBlock{0, 0, 0}};
+  double one = 1.0;
+  v.data.upload(&one, 1, s);
+  v.n_elems = 1;
+  v.index_by_in();
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------
+// superblock at position p: enlarged operators, wave-function layout, H_eff task lists
+// ---------------------------------------------------------------------------------------
+static void build_super(Ctx& c, int p) {
+  DMRG_REQUIRE(c.built, DMRG_EINVAL, "dmrg_build_blocks has not been called");
+  DMRG_REQUIRE(p >= 1 && p <= c.N - 3, DMRG_EINVAL, "position out of range [1, N-3]");
+  DMRG_REQUIRE(c.left[p - 1].valid && c.right[p + 1].valid, DMRG_EINVAL,
+               "blocks for this position are not available");
+  auto sb = std::make_unique<Super>();
+  sb->p = p;
+  enlarge(c, c.left[p - 1].ops, p, true, sb->Ll, sb->L);
+  enlarge(c, c.right[p + 1].ops, p + 1, false, sb->Rl, sb->R);
+  const QN T = c.chain.target;
+  const int nL = sb->Ll.sec.size(), nR = sb->Rl.sec.size();
+  sb->psi_of_L.assign(nL, -1);
+  sb->psi_of_R.assign(nR, -1);
+  int64_t off = 0;
+  for (int i = 0; i < nL; ++i) {
+    int j = sb->Rl.sec.find(T - sb->Ll.sec.q[i]);
+    if (j < 0) continue;
+    sb->psi_of_L[i] = int(sb->bL.size());
+    sb->psi_of_R[j] = int(sb->bL.size());
+    sb->bL.push_back(i);
+    sb->bR.push_back(j);
+    sb->bdl.push_back(sb->Ll.sec.d[i]);
+    sb->bdr.push_back(sb->Rl.sec.d[j]);
+    sb->boff.push_back(off);
+    off += int64_t(sb->Ll.sec.d[i]) * sb->Rl.sec.d[j];
+  }
+  sb->size = off;
+  // H_eff items: (label k, L block, R block)
+  const auto& par = c.mpo.parity[p + 1];
+  const int nlab = sb->L.nlab;
+  DMRG_REQUIRE(nlab == sb->R.nlab, DMRG_EINVAL, "internal: label count mismatch");
+  struct Item {
+    int64_t lb, rb;
+    int bin, bout;
+    double sign;
+  };
+  std::vector<std::vector<Item>> by_out(sb->bL.size());
+  std::vector<char> lused(sb->L.blocks.size(), 0), rused(sb->R.blocks.size(), 0);
+  for (int k = 0; k < nlab; ++k) {
+    for (int64_t x = sb->L.lab_ptr[k]; x < sb->L.lab_ptr[k + 1]; ++x) {
+      const OpBlock& lb = sb->L.blocks[x];
+      const int bin = sb->psi_of_L[lb.si], bout = sb->psi_of_L[lb.so];
+      if (bin < 0 || bout < 0) continue;
+      const int rb = sb->R.by_in[size_t(k) * nR + sb->bR[bin]];
+      if (rb < 0) continue;
+      DMRG_REQUIRE(sb->R.blocks[rb].so == sb->bR[bout], DMRG_EINVAL,
+                   "internal: superblock term breaks the target sector");
+      double sign = (par[k] && (particles(sb->Ll.sec.q[lb.si]) & 1)) ? -1.0 : 1.0;
+      by_out[bout].push_back(Item{x, rb, bin, bout, sign});
+      lused[x] = 1;
+      rused[rb] = 1;
+    }
+  }
+  TaskList s1, s2;
+  int64_t toff = 0;
+  double flops = 0;
+  int64_t items = 0;
+  for (size_t bo = 0; bo < by_out.size(); ++bo) {
+    if (by_out[bo].empty()) continue;
+    const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
+    s2.begin_task(Operand{sb->boff[bo], B_Y, dRo}, dLo, dRo);
+    for (const Item& it : by_out[bo]) {
+      const int dLi = sb->bdl[it.bin], dRi = sb->bdr[it.bin];
+      const OpBlock& lb = sb->L.blocks[it.lb];
+      const OpBlock& rb = sb->R.blocks[it.rb];
+      s1.begin_task(Operand{toff, B_T, dRo}, dLi, dRo);
+      s1.add_term(Operand{sb->boff[it.bin], B_X, dRi}, Operand{rb.off, B_ROPS, dRi}, dRi, 2, 1.0);
+      s2.add_term(Operand{lb.off, B_LOPS, dLi}, Operand{toff, B_T, dRo}, dLi, 0, it.sign);
+      toff += int64_t(dLi) * dRo;
+      double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;
+      double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;
+      flops += std::min(f1, f2);
+      ++items;
+    }
+  }
+  sb->t_elems = toff;
+  sb->n_items = items;
+  sb->flops = flops;
+  double bytes = 0;
+  for (size_t x = 0; x < lused.size(); ++x)
+    if (lused[x]) bytes += double(sb->Ll.sec.d[sb->L.blocks[x].so]) * sb->Ll.sec.d[sb->L.blocks[x].si];
+  for (size_t x = 0; x < rused.size(); ++x)
+    if (rused[x]) bytes += double(sb->Rl.sec.d[sb->R.blocks[x].so]) * sb->Rl.sec.d[sb->R.blocks[x].si];
+  bytes += 2.0 * double(sb->size);
+  sb->bytes = bytes * (c.opt.precision == DMRG_FP64 ? 8.0 : 4.0);
+  {
+    int64_t be[NBASE] = {0};
+    be[B_X] = sb->size;
+    be[B_Y] = sb->size;
+    be[B_T] = sb->t_elems;
+    be[B_LOPS] = sb->L.n_elems;
+    be[B_ROPS] = sb->R.n_elems;
+    sb->st1.build(s1, be, c.stream);
+    sb->st2.build(s2, be, c.stream);
+  }
+  // diagonal tasks: terms that keep the sector (Delta q = 0)
+  std::vector<DiagTask> dt;
+  std::vector<DiagTerm> dg;
+  std::vector<int> diag_labels;
+  for (int k = 0; k < nlab; ++k) {
+    const QN& d = c.mpo.dq[p + 1][k];
+    if (d.a == 0 && d.b == 0 && d.m == 0) diag_labels.push_back(k);
+  }
+  for (size_t b = 0; b < sb->bL.size(); ++b) {
+    DiagTask t;
+    t.psi_off = sb->boff[b];
+    t.dL = sb->bdl[b];
+    t.dR = sb->bdr[b];
+    t.t0 = int(dg.size());
+    for (int k : diag_labels) {
+      int lb = sb->L.by_in[size_t(k) * nL + sb->bL[b]];
+      int rb = sb->R.by_in[size_t(k) * nR + sb->bR[b]];
+      if (lb < 0 || rb < 0) continue;
+      dg.push_back(DiagTerm{sb->L.blocks[lb].off, sb->R.blocks[rb].off, t.dL, t.dR});
+    }
+    t.t1 = int(dg.size());
+    dt.push_back(t);
+  }
+  sb->dtasks.upload(dt, c.stream);
+  sb->dterms.upload(dg, c.stream);
+  sb->n_dtasks = int(dt.size());
+  if (c.opt.precision != DMRG_FP64) {
+    sb->L.data32.alloc(std::max<int64_t>(sb->L.n_elems, 1));
+    sb->R.data32.alloc(std::max<int64_t>(sb->R.n_elems, 1));
+    to_f32(sb->L.data.p, sb->L.data32.p, sb->L.n_elems, c.stream);
+    to_f32(sb->R.data.p, sb->R.data32.p, sb->R.n_elems, c.stream);
+  }
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  c.sb = std::move(sb);
+}
+
+static Super& super_at(Ctx& c, int p) {
+  if (!c.sb || c.sb->p != p) build_super(c, p);
+  return *c.sb;
+}
+
+static void heff(Ctx& c, Super& sb, const double* x, double* y) {
+  c.T.alloc(std::max<int64_t>(sb.t_elems, 1));
+  if (c.opt.precision == DMRG_FP64) {
+    DMRG_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * sb.size, c.stream));
+    Bases<double> b{};
+    b.p[B_LOPS] = sb.L.data.p;
+    b.p[B_ROPS] = sb.R.data.p;
+    b.p[B_X] = const_cast<double*>(x);
+    b.p[B_Y] = y;
+    b.p[B_T] = c.T.p;
+    run_gemm_tasks<double>(sb.st1, b, 1, c.stream);
+    run_gemm_tasks<double>(sb.st2, b, 1, c.stream);
+  } else {
+    c.f32a.alloc(std::max<int64_t>(sb.size, 1));
+    c.f32b.alloc(std::max<int64_t>(sb.size, 1));
+    c.f32T.alloc(std::max<int64_t>(sb.t_elems, 1));
+    to_f32(x, c.f32a.p, sb.size, c.stream);
+    DMRG_CUDA(cudaMemsetAsync(c.f32b.p, 0, sizeof(float) * sb.size, c.stream));
+    Bases<float> b{};
+    b.p[B_LOPS] = sb.L.data32.p;
+    b.p[B_ROPS] = sb.R.data32.p;
+    b.p[B_X] = c.f32a.p;
+    b.p[B_Y] = c.f32b.p;
+    b.p[B_T] = c.f32T.p;
+    run_gemm_tasks<float>(sb.st1, b, 1, c.stream);
+    run_gemm_tasks<float>(sb.st2, b, 1, c.stream);
+    to_f64(c.f32b.p, y, sb.size, c.stream);
+  }
+}
+
+// FP64 product regardless of the context precision (energy of the mixed path)
+static void heff64(Ctx& c, Super& sb, const double* x, double* y) {
+  int keep = c.opt.precision;
+  c.opt.precision = DMRG_FP64;
+  try {
+    heff(c, sb, x, y);
+  } catch (...) {
+    c.opt.precision = keep;
+    throw;
+  }
+  c.opt.precision = keep;
+}
+
+static void ensure_diag(Ctx& c, Super& sb) {
+  if (sb.diag_ready) return;
+  sb.diag.alloc(std::max<int64_t>(sb.size, 1));
+  heff_diag(sb.dtasks.p, sb.n_dtasks, sb.dterms.p, sb.L.data.p, sb.R.data.p, sb.diag.p, c.stream);
+  sb.diag_ready = true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Davidson
+// ---------------------------------------------------------------------------------------
+__global__ void k_set_hs_diag(double* H, int ld, const double* w) {
+  if (threadIdx.x == 0) {
+    H[0] = w[0];
+    H[1] = 0.0;
+    H[ld] = 0.0;
+    H[ld + 1] = w[1];
+  }
+}
+
+static void ensure_ws(Ctx& c, int64_t n, int sub) {
+  if (c.ws_n >= n && c.ws_sub >= sub) return;
+  int64_t nn = std::max<int64_t>(n, 1);
+  c.V.alloc(nn * sub);
+  c.AV.alloc(nn * sub);
+  c.r.alloc(nn);
+  c.t.alloc(nn);
+  c.x.alloc(nn);
+  c.Ax.alloc(nn);
+  c.x1.alloc(nn);
+  c.Ax1.alloc(nn);
+  c.small.alloc(64 * 64 * 6 + 1024);
+  c.partials.alloc(64 * 300);
+  std::vector<const double*> ptrs(2 * sub);
+  for (int j = 0; j < sub; ++j) {
+    ptrs[j] = c.V.p + j * nn;
+    ptrs[sub + j] = c.AV.p + j * nn;
+  }
+  c.vptr.upload(ptrs, c.stream);
+  c.ws_n = nn;
+  c.ws_sub = sub;
+}
+
+struct DavResult {
+  double theta = 0, resid = 0;
+  int nprod = 0;
+  bool converged = false;
+};
+
+static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
+  const int64_t n = sb.size;
+  const int sub = std::max(4, std::min(64, c.opt.dav_max_sub));
+  ensure_ws(c, n, sub);
+  ensure_diag(c, sb);
+  cudaStream_t s = c.stream;
+  double* Hs = c.small.p;               // 64 x 64, row k holds <v_i, H v_k>, i <= k
+  double* w = Hs + 64 * 64;             // Ritz values, ascending
+  double* Y = w + 64;                   // 64 x 64, row j = coefficients of the j-th Ritz vector
+  double* scr = Y + 64 * 64;            // 2 x 64 x 64 scratch for the Ritz solve
+  double* sc = scr + 2 * 64 * 64;       // device scalars
+  double* part = c.partials.p;
+  const double* const* Vp = c.vptr.p;
+  const double* const* AVp = c.vptr.p + sub;
+  const int64_t ld = c.ws_n;
+  auto vec = [&](int j) { return c.V.p + j * ld; };
+  auto avec = [&](int j) { return c.AV.p + j * ld; };
+  auto readback = [&](const double* d, int cnt, double* h) {
+    DMRG_CUDA(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    DMRG_CUDA(cudaStreamSynchronize(s));
+  };
+  auto d2d = [&](double* dst, const double* src) {
+    DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  };
+  // v_0 = x0 / |x0|
+  d2d(vec(0), guess);
+  dot(vec(0), vec(0), n, sc, part, s);
+  scale_vec(vec(0), n, sc, 1, s);
+  heff(c, sb, vec(0), avec(0));
+  int nprod = 1, k = 1;
+  multidot(Vp, 1, avec(0), n, Hs, part, s);
+  DavResult res;
+  const double tol = c.opt.dav_tol;
+  double h[4];
+  while (true) {
+    // Ritz pair of the projected matrix, residual r = H x - theta x
+    ritz_solve(Hs, 64, k, scr, w, Y, s);
+    lincomb(Vp, Y, k, n, c.x.p, 0.0, 1.0, s);
+    lincomb(AVp, Y, k, n, c.Ax.p, 0.0, 1.0, s);
+    davidson_residual(c.x.p, c.Ax.p, w, n, c.r.p, s);
+    dot(c.r.p, c.r.p, n, sc + 1, part, s);
+    DMRG_CUDA(cudaMemcpyAsync(sc, w, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    readback(sc, 2, h);
+    const double theta = h[0], rn = std::sqrt(std::max(h[1], 0.0));
+    res.theta = theta;
+    res.resid = rn;
+    res.nprod = nprod;
+    if (rn <= tol || nprod >= c.opt.dav_max_iter) {
+      res.converged = rn <= tol;
+      break;
+    }
+    // correction t = r / (theta - D), clamped
+    davidson_correction(c.r.p, sb.diag.p, w, n, c.t.p, s);
+    if (k >= sub) {   // thick restart from the two lowest Ritz vectors
+      lincomb(Vp, Y + 64, k, n, c.x1.p, 0.0, 1.0, s);
+      lincomb(AVp, Y + 64, k, n, c.Ax1.p, 0.0, 1.0, s);
+      d2d(vec(0), c.x.p);
+      d2d(vec(1), c.x1.p);
+      d2d(avec(0), c.Ax.p);
+      d2d(avec(1), c.Ax1.p);
+      k_set_hs_diag<<<1, 32, 0, s>>>(Hs, 64, w);
+      DMRG_CUDA(cudaGetLastError());
+      k = 2;
+    }
+    dot(c.t.p, c.t.p, n, sc + 2, part, s);
+    for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+      multidot(Vp, k, c.t.p, n, sc + 32, part, s);
+      lincomb(Vp, sc + 32, k, n, c.t.p, 1.0, -1.0, s);
+    }
+    dot(c.t.p, c.t.p, n, sc + 3, part, s);
+    readback(sc + 2, 2, h);
+    const double tn0 = std::sqrt(std::max(h[0], 0.0)), tn = std::sqrt(std::max(h[1], 0.0));
+    if (tn <= 1e-14 * std::max(tn0, 1e-300)) break;   // no new direction left
+    d2d(vec(k), c.t.p);
+    scale_vec(vec(k), n, sc + 3, 1, s);
+    heff(c, sb, vec(k), avec(k));
+    ++nprod;
+    multidot(Vp, k + 1, avec(k), n, Hs + 64 * k, part, s);
+    ++k;
+  }
+  dot(c.x.p, c.x.p, n, sc + 4, part, s);
+  scale_vec(c.x.p, n, sc + 4, 1, s);
+  if (c.opt.precision != DMRG_FP64) {
+    // energy of the mixed path: FP64 Rayleigh quotient of the converged vector
+    heff64(c, sb, c.x.p, c.Ax.p);
+    dot(c.x.p, c.Ax.p, n, sc + 5, part, s);
+    readback(sc + 5, 1, h);
+    res.theta = h[0];
+  }
+  d2d(out, c.x.p);
+  DMRG_CUDA(cudaStreamSynchronize(s));
+  return res;
+}
+
+
+// ---------------------------------------------------------------------------------------
+// truncation by the reduced density matrix and renormalization of the new block
+// ---------------------------------------------------------------------------------------
+struct TruncResult {
+  double trunc = 0.0;
+  int kept = 0;
+};
+
+static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
+  DMRG_REQUIRE(c.sb && c.sb->p == p && c.psi_valid && c.psi_p == p, DMRG_EINVAL,
+               "no eigenvector held for this position (call dmrg_davidson first)");
+  DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
+  DMRG_REQUIRE(M >= 1, DMRG_EINVAL, "M must be positive");
+  Super& sb = *c.sb;
+  cudaStream_t s = c.stream;
+  const Layout& lay = dir == 0 ? sb.Ll : sb.Rl;
+  const int ns = lay.sec.size();
+  int64_t total = 0, sq = 0;
+  std::vector<int64_t> roff(ns), woff(ns);
+  std::vector<int32_t> dims(ns);
+  for (int i = 0; i < ns; ++i) {
+    roff[i] = sq;
+    woff[i] = total;
+    dims[i] = lay.sec.d[i];
+    sq += int64_t(lay.sec.d[i]) * lay.sec.d[i];
+    total += lay.sec.d[i];
+  }
+  Iso iso;
+  TruncResult tr;
+  if (total <= M) {
+    identity_iso(c, lay, iso);
+    tr.trunc = 0.0;
+    tr.kept = int(total);
+  } else {
+    TaskList R;
+    for (size_t b = 0; b < sb.bL.size(); ++b) {
+      const int dL = sb.bdl[b], dR = sb.bdr[b];
+      if (dir == 0) {
+        const int Q = sb.bL[b];
+        R.begin_task(Operand{roff[Q], B_Y, dL}, dL, dL);
+        R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dR, 2, 1.0);
+      } else {
+        const int Q = sb.bR[b];
+        R.begin_task(Operand{roff[Q], B_Y, dR}, dR, dR);
+        R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dL, 1, 1.0);
+      }
+    }
+    c.rho.alloc(sq);
+    c.eV.alloc(sq);
+    c.eVs.alloc(sq);
+    c.ew.alloc(total);
+    int64_t np2 = 1;
+    while (np2 < total) np2 <<= 1;
+    c.sel.alloc(np2 + 4 * int64_t(ns) + 16);
+    DMRG_CUDA(cudaMemsetAsync(c.rho.p, 0, sizeof(double) * sq, s));
+    DevTaskList dR;
+    {
+      int64_t be[NBASE] = {0};
+      be[B_X] = sb.size;
+      be[B_Y] = sq;
+      dR.build(R, be, s);
+    }
+    Bases<double> bb{};
+    bb.p[B_X] = c.psi.p;
+    bb.p[B_Y] = c.rho.p;
+    run_gemm_tasks<double>(dR, bb, 1, s);
+    int maxd = 0;
+    for (int x : dims) maxd = std::max(maxd, x);
+    DMRG_REQUIRE(maxd <= 1024, DMRG_EINVAL, "sector dimension above 1024 not supported");
+    DevBuf<int64_t> droff, dwoff, duoff;
+    DevBuf<int32_t> ddim, dkept;
+    droff.upload(roff, s);
+    dwoff.upload(woff, s);
+    ddim.upload(dims, s);
+    batched_eigh2(droff.p, dwoff.p, ddim.p, ns, c.rho.p, c.eV.p, c.eVs.p, c.ew.p, 1, 1, s);
+    double* lamM = c.sel.p + np2;
+    double* kw = lamM + 8;
+    kth_largest(c.ew.p, total, M, c.sel.p, lamM, s);
+    dkept.alloc(ns);
+    count_kept(dwoff.p, ddim.p, ns, c.ew.p, lamM, dkept.p, kw, s);
+    std::vector<int32_t> kept(ns);
+    std::vector<double> kwh(ns);
+    DMRG_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s));
+    DMRG_CUDA(cudaMemcpyAsync(kwh.data(), kw, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    DMRG_CUDA(cudaStreamSynchronize(s));
+    iso.lay = lay;
+    iso.m.assign(ns, 0);
+    iso.uoff.assign(ns, 0);
+    int64_t uo = 0;
+    double kept_w = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      iso.m[i] = kept[i];
+      iso.uoff[i] = uo;
+      uo += int64_t(dims[i]) * kept[i];
+      tr.kept += kept[i];
+      kept_w += kwh[i];
+    }
+    tr.trunc = std::max(0.0, 1.0 - kept_w);
+    iso.data.alloc(std::max<int64_t>(uo, 1));
+    duoff.upload(iso.uoff, s);
+    gather_u(droff.p, ddim.p, dkept.p, duoff.p, ns, c.eVs.p, iso.data.p, s);
+    DMRG_CUDA(cudaStreamSynchronize(s));
+    iso.identity = false;
+  }
+  finish_iso_index(iso);
+  Blk& dst = dir == 0 ? c.left[p] : c.right[p];
+  dst.valid = false;
+  OpSet ops;
+  project(c, dir == 0 ? sb.L : sb.R, iso, ops);
+  dst.ops = std::move(ops);
+  dst.iso = std::move(iso);
+  dst.valid = true;
+  c.prev = std::move(c.sb);   // layouts of the superblock psi belongs to
+  return tr;
+}
+
+// ---------------------------------------------------------------------------------------
+// prediction of the next wave function (White's transformation)
+// ---------------------------------------------------------------------------------------
+static void uniform_guess(Ctx& c, Super& sb, double* g) {
+  fill_value(g, sb.size, 1.0 / std::sqrt(double(std::max<int64_t>(sb.size, 1))), c.stream);
+}
+
+static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
+  cudaStream_t s = c.stream;
+  if (!c.psi_valid || !c.prev) {
+    uniform_guess(c, sb, g);
+    return;
+  }
+  Super& pr = *c.prev;
+  if (pr.p == p) {
+    DMRG_REQUIRE(pr.size == sb.size, DMRG_EINVAL, "internal: layout changed at turn");
+    DMRG_CUDA(cudaMemcpyAsync(g, c.psi.p, sizeof(double) * sb.size, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  TaskList A, B;
+  int64_t xoff = 0;
+  int64_t bu_n = 0, bv_n = 0;
+  Bases<double> bb{};
+  if (dir == 0 && pr.p == p - 1) {
+    const Iso& U = c.left[p - 1].iso;     // new left block of bond p-1
+    const Iso& Ur = c.right[p].iso;       // right block of bond p: (site p+1) x (right of p+1)
+    const SectorSet& lsec = c.left[p - 1].ops.sec;
+    const SectorSet& rsec = c.right[p].ops.sec;
+    DMRG_REQUIRE(Ur.lay.sec.q == sb.Rl.sec.q && Ur.lay.sec.d == sb.Rl.sec.d, DMRG_EINVAL,
+                 "internal: right basis does not refer to the current enlarged space");
+    for (size_t b = 0; b < pr.bL.size(); ++b) {
+      const int QLo = pr.bL[b], QRo = pr.bR[b], dL = pr.bdl[b], dR = pr.bdr[b];
+      const int newl = U.kept_idx[QLo];
+      if (newl < 0) continue;
+      const int m = U.m[QLo];
+      A.begin_task(Operand{xoff, B_T, dR}, m, dR);
+      A.add_term(Operand{U.uoff[QLo], B_U, m}, Operand{pr.boff[b], B_X, dR}, dL, 1, 1.0);
+      for (int sg = 0; sg < 2; ++sg) {
+        const int rb = pr.Rl.pblk[QRo][sg];
+        if (rb < 0) continue;
+        const int coff = pr.Rl.poff[QRo][sg], dr = rsec.d[rb];
+        const int er = Ur.enl_idx[rb];
+        QN qn = sg ? lsec.q[newl] + c.chain.q[p] : lsec.q[newl];
+        const int QLn = sb.Ll.sec.find(qn);
+        if (QLn < 0 || sb.Ll.pblk[QLn][sg] != newl) continue;
+        const int bn = sb.psi_of_L[QLn];
+        if (bn < 0 || sb.bR[bn] != er) continue;
+        const int rof = sb.Ll.poff[QLn][sg], dRn = sb.bdr[bn];
+        B.begin_task(Operand{sb.boff[bn] + int64_t(rof) * dRn, B_Y, dRn}, m, dRn);
+        B.add_term(Operand{xoff + coff, B_T, dR}, Operand{Ur.uoff[er], B_V, dr}, dr, 2, 1.0);
+      }
+      xoff += int64_t(m) * dR;
+    }
+    bb.p[B_U] = U.data.p;
+    bb.p[B_V] = Ur.data.p;
+    bu_n = U.data.n;
+    bv_n = Ur.data.n;
+  } else if (dir == 1 && pr.p == p + 1) {
+    const Iso& V = c.right[p + 1].iso;    // new right block of bond p+1
+    const Iso& Ul = c.left[p].iso;        // left block of bond p: (left of p-1) x (site p)
+    const SectorSet& rsec = c.right[p + 1].ops.sec;
+    const SectorSet& lsec = c.left[p].ops.sec;
+    DMRG_REQUIRE(Ul.lay.sec.q == sb.Ll.sec.q && Ul.lay.sec.d == sb.Ll.sec.d, DMRG_EINVAL,
+                 "internal: left basis does not refer to the current enlarged space");
+    for (size_t b = 0; b < pr.bL.size(); ++b) {
+      const int QLo = pr.bL[b], QRo = pr.bR[b], dL = pr.bdl[b], dR = pr.bdr[b];
+      const int newr = V.kept_idx[QRo];
+      if (newr < 0) continue;
+      const int m = V.m[QRo];
+      A.begin_task(Operand{xoff, B_T, m}, dL, m);
+      A.add_term(Operand{pr.boff[b], B_X, dR}, Operand{V.uoff[QRo], B_U, m}, dR, 0, 1.0);
+      for (int sg = 0; sg < 2; ++sg) {
+        const int lb = pr.Ll.pblk[QLo][sg];
+        if (lb < 0) continue;
+        const int roff = pr.Ll.poff[QLo][sg], dl = lsec.d[lb];
+        const int el = Ul.enl_idx[lb];
+        QN qn = sg ? rsec.q[newr] + c.chain.q[p + 1] : rsec.q[newr];
+        const int QRn = sb.Rl.sec.find(qn);
+        if (QRn < 0 || sb.Rl.pblk[QRn][sg] != newr) continue;
+        const int bn = sb.psi_of_L[el];
+        if (bn < 0 || sb.bR[bn] != QRn) continue;
+        const int cof = sb.Rl.poff[QRn][sg], dRn = sb.bdr[bn];
+        B.begin_task(Operand{sb.boff[bn] + cof, B_Y, dRn}, sb.bdl[bn], m);
+        B.add_term(Operand{Ul.uoff[el], B_V, dl}, Operand{xoff + int64_t(roff) * m, B_T, m}, dl,
+                   0, 1.0);
+      }
+      xoff += int64_t(dL) * m;
+    }
+    bb.p[B_U] = V.data.p;
+    bb.p[B_V] = Ul.data.p;
+    bu_n = V.data.n;
+    bv_n = Ul.data.n;
+  } else {
+    uniform_guess(c, sb, g);
+    return;
+  }
+  c.tmp.alloc(std::max<int64_t>(xoff, 1));
+  DMRG_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * sb.size, s));
+  DevTaskList dA, dB;
+  {
+    int64_t be[NBASE] = {0};
+    be[B_X] = pr.size;
+    be[B_T] = c.tmp.n;
+    be[B_Y] = sb.size;
+    be[B_U] = bu_n;
+    be[B_V] = bv_n;
+    dA.build(A, be, s);
+    dB.build(B, be, s);
+  }
+  bb.p[B_X] = c.psi.p;
+  bb.p[B_T] = c.tmp.p;
+  bb.p[B_Y] = g;
+  run_gemm_tasks<double>(dA, bb, 1, s);
+  run_gemm_tasks<double>(dB, bb, 1, s);
+  c.small.alloc(64 * 64 * 6 + 1024);
+  c.partials.alloc(64 * 300);
+  double* sc = c.small.p + 64 * 64 * 6;
+  dot(g, g, sb.size, sc, c.partials.p, s);
+  double nrm2 = 0;
+  DMRG_CUDA(cudaMemcpyAsync(&nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DMRG_CUDA(cudaStreamSynchronize(s));
+  if (!(nrm2 > 0.0)) {
+    uniform_guess(c, sb, g);
+    return;
+  }
+  scale_vec(g, sb.size, sc, 1, s);
+}
+
+// ---------------------------------------------------------------------------------------
+// blocks from the starting state
+// ---------------------------------------------------------------------------------------
+static void build_blocks(Ctx& c, const dmrg_mps_init* init) {
+  const int N = c.N;
+  cudaStream_t s = c.stream;
+  c.left.clear();
+  c.right.clear();
+  c.left.resize(N);
+  c.right.resize(N);
+  c.sb.reset();
+  c.prev.reset();
+  c.psi_valid = false;
+  c.built = false;
+  {
+    OpSet vac = vacuum_ops(int(c.mpo.labels[0].size()), 0, s);
+    Layout lay;
+    OpSet E;
+    enlarge(c, vac, 0, true, lay, E);
+    identity_iso(c, lay, c.left[0].iso);
+    project(c, E, c.left[0].iso, c.left[0].ops);
+    c.left[0].valid = true;
+  }
+  {
+    OpSet vac = vacuum_ops(int(c.mpo.labels[N].size()), 0, s);
+    Layout lay;
+    OpSet E;
+    enlarge(c, vac, N - 1, false, lay, E);
+    identity_iso(c, lay, c.right[N - 2].iso);
+    project(c, E, c.right[N - 2].iso, c.right[N - 2].ops);
+    c.right[N - 2].valid = true;
+  }
+  DMRG_REQUIRE(init != nullptr, DMRG_EINVAL, "starting state is NULL");
+  DMRG_REQUIRE(init->n_bonds == N - 4, DMRG_EINVAL, "starting state must cover bonds N-3..2");
+  for (int bi = 0; bi < init->n_bonds; ++bi) {
+    const int b = init->bonds[bi];
+    DMRG_REQUIRE(b == N - 3 - bi, DMRG_EINVAL, "starting state bonds must be N-3, N-4, ..., 2");
+    Layout lay;
+    OpSet E;
+    enlarge(c, c.right[b + 1].ops, b + 1, false, lay, E);
+    Iso iso;
+    iso.lay = lay;
+    const int ns = lay.sec.size();
+    iso.m.assign(ns, 0);
+    iso.uoff.assign(ns, 0);
+    std::vector<int64_t> src(ns, -1);
+    for (int x = init->bond_ptr[bi]; x < init->bond_ptr[bi + 1]; ++x) {
+      const int32_t* r = init->sec + 5 * int64_t(x);
+      QN q{r[0], r[1], r[2]};
+      const int idx = lay.sec.find(q);
+      DMRG_REQUIRE(idx >= 0 && lay.sec.d[idx] == r[3] && r[4] >= 0 && r[4] <= r[3], DMRG_EINVAL,
+                   "starting state does not match the sector structure at bond " +
+                       std::to_string(b));
+      DMRG_REQUIRE(init->u_off[x + 1] - init->u_off[x] == int64_t(r[3]) * r[4], DMRG_EINVAL,
+                   "starting state isometry size mismatch");
+      iso.m[idx] = r[4];
+      src[idx] = init->u_off[x];
+    }
+    int64_t uo = 0;
+    for (int i = 0; i < ns; ++i) {
+      iso.uoff[i] = uo;
+      uo += int64_t(lay.sec.d[i]) * iso.m[i];
+    }
+    std::vector<double> h(std::max<int64_t>(uo, 1), 0.0);
+    for (int i = 0; i < ns; ++i)
+      if (iso.m[i] > 0)
+        std::memcpy(h.data() + iso.uoff[i], init->u + src[i],
+                    sizeof(double) * size_t(lay.sec.d[i]) * iso.m[i]);
+    iso.data.upload(h, s);
+    finish_iso_index(iso);
+    OpSet ops;
+    project(c, E, iso, ops);
+    c.right[b].ops = std::move(ops);
+    c.right[b].iso = std::move(iso);
+    c.right[b].valid = true;
+  }
+  c.built = true;
+}
+
+// ---------------------------------------------------------------------------------------
+// one two-site step
+// ---------------------------------------------------------------------------------------
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
+  double t0 = now_s();
+  Super& sb = super_at(c, p);
+  c.psi_guess.alloc(std::max<int64_t>(sb.size, 1));
+  predict(c, sb, p, dir, c.psi_guess.p);
+  c.psi.alloc(std::max<int64_t>(sb.size, 1));
+  DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p);
+  c.psi_valid = true;
+  c.psi_p = p;
+  TruncResult tr = truncate_renormalize(c, p, dir, M);
+  if (st) {
+    st->p = p;
+    st->dir = dir;
+    st->n_products = r.nprod;
+    st->kept = tr.kept;
+    st->energy = r.theta;
+    st->residual = r.resid;
+    st->trunc_err = tr.trunc;
+    st->seconds = now_s() - t0;
+  }
+}
+
+}  // namespace dmrg
+
+// =======================================================================================
+// C-ABI
+// =======================================================================================
+using namespace dmrg;
+
+template <class F>
+static int guarded(dmrg_ctx* c, F&& f) {
+  if (!c) return DMRG_EINVAL;
+  try {
+    f();
+    return DMRG_OK;
+  } catch (const Error& e) {
+    c->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return DMRG_ENOMEM;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return DMRG_EINVAL;
+  }
+}
+
+extern "C" int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dmrg_ctx** out) {
+  if (!out) return DMRG_EINVAL;
+  *out = nullptr;
+  dmrg_ctx* c = nullptr;
+  try {
+    c = new dmrg_ctx();
+  } catch (...) {
+    return DMRG_ENOMEM;
+  }
+  int st = guarded(c, [&] {
+    DMRG_REQUIRE(opt != nullptr, DMRG_EINVAL, "options are NULL");
+    c->opt = *opt;
+    DMRG_REQUIRE(opt->precision == DMRG_FP64 || opt->precision == DMRG_MIXED_FP32, DMRG_EINVAL,
+                 "unknown precision");
+    DMRG_REQUIRE(opt->dav_tol > 0 && opt->dav_max_iter >= 1 && opt->dav_max_sub >= 4 &&
+                     opt->dav_max_sub <= 64,
+                 DMRG_EINVAL, "bad Davidson options");
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+    build_chain(prob, c->chain);
+    build_mpo(c->chain, c->mpo);
+    c->N = c->chain.N;
+    build_reach(*c);
+    c->w_by_b.resize(c->N);
+    c->w_by_a.resize(c->N);
+    for (int s = 0; s < c->N; ++s) {
+      const auto& W = c->mpo.W[s];
+      std::vector<int> idx(W.size());
+      for (size_t i = 0; i < W.size(); ++i) idx[i] = int(i);
+      c->w_by_b[s] = idx;
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return W[x].a < W[y].a; });
+      c->w_by_a[s] = idx;
+      for (size_t i = 1; i < W.size(); ++i)
+        DMRG_REQUIRE(W[i].b >= W[i - 1].b, DMRG_EINVAL, "internal: entries not grouped");
+    }
+  });
+  if (st != DMRG_OK) {
+    // keep the context so that the caller can read the message, as documented
+    *out = c;
+    return st;
+  }
+  *out = c;
+  return DMRG_OK;
+}
+
+extern "C" int dmrg_destroy(dmrg_ctx* c) {
+  if (!c) return DMRG_OK;
+  delete c;
+  return DMRG_OK;
+}
+
+extern "C" const char* dmrg_last_error(const dmrg_ctx* c) {
+  return c ? c->err.c_str() : "NULL context";
+}
+
+extern "C" int dmrg_build_blocks(dmrg_ctx* c, const dmrg_mps_init* init) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(c->N > 0, DMRG_EINVAL, "context was not created successfully");
+    build_blocks(*c, init);
+  });
+}
+
+extern "C" int dmrg_psi_layout(dmrg_ctx* c, int32_t p, int64_t* n_blocks, int64_t* size,
+                               int32_t* qn_left, int32_t* dl, int32_t* dr, int64_t* off) {
+  return guarded(c, [&] {
+    Super& sb = super_at(*c, p);
+    if (n_blocks) *n_blocks = int64_t(sb.bL.size());
+    if (size) *size = sb.size;
+    for (size_t b = 0; b < sb.bL.size(); ++b) {
+      if (qn_left) {
+        const QN& q = sb.Ll.sec.q[sb.bL[b]];
+        qn_left[3 * b] = q.a;
+        qn_left[3 * b + 1] = q.b;
+        qn_left[3 * b + 2] = q.m;
+      }
+      if (dl) dl[b] = sb.bdl[b];
+      if (dr) dr[b] = sb.bdr[b];
+      if (off) off[b] = sb.boff[b];
+    }
+  });
+}
+
+extern "C" int dmrg_heff_apply(dmrg_ctx* c, int32_t p, const double* x, double* y) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(x && y && x != y, DMRG_EINVAL, "bad vectors");
+    Super& sb = super_at(*c, p);
+    heff(*c, sb, x, y);
+    DMRG_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+extern "C" int dmrg_davidson(dmrg_ctx* c, int32_t p, const double* guess, double* out,
+                             double* energy, dmrg_dav_stats* st) {
+  int conv = 1;
+  int rc = guarded(c, [&] {
+    double t0 = now_s();
+    Super& sb = super_at(*c, p);
+    c->psi_guess.alloc(std::max<int64_t>(sb.size, 1));
+    if (guess) {
+      DMRG_CUDA(cudaMemcpyAsync(c->psi_guess.p, guess, sizeof(double) * sb.size,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      predict(*c, sb, p, (c->prev && c->prev->p > p) ? 1 : 0, c->psi_guess.p);
+    }
+    c->psi.alloc(std::max<int64_t>(sb.size, 1));
+    DavResult r = davidson(*c, sb, c->psi_guess.p, c->psi.p);
+    c->psi_valid = true;
+    c->psi_p = p;
+    if (out) {
+      DMRG_CUDA(cudaMemcpyAsync(out, c->psi.p, sizeof(double) * sb.size, cudaMemcpyDeviceToDevice,
+                                c->stream));
+      DMRG_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    if (energy) *energy = r.theta;
+    if (st) {
+      st->n_products = r.nprod;
+      st->converged = r.converged ? 1 : 0;
+      st->residual = r.resid;
+      st->energy = r.theta;
+      st->heff_flops = sb.flops;
+      st->heff_bytes = sb.bytes;
+      st->seconds = now_s() - t0;
+    }
+    conv = r.converged ? 1 : 0;
+  });
+  if (rc == DMRG_OK && !conv) {
+    c->err = "Davidson did not reach the tolerance within dav_max_iter products";
+    return DMRG_ENOCONV;
+  }
+  return rc;
+}
+
+extern "C" int dmrg_truncate_renormalize(dmrg_ctx* c, int32_t p, int32_t dir, int32_t M,
+                                         double* trunc_err, int32_t* kept) {
+  return guarded(c, [&] {
+    TruncResult tr = truncate_renormalize(*c, p, dir, M);
+    if (trunc_err) *trunc_err = tr.trunc;
+    if (kept) *kept = tr.kept;
+  });
+}
+
+extern "C" int dmrg_step(dmrg_ctx* c, int32_t p, int32_t dir, int32_t M, dmrg_step_stats* st) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
+    step(*c, p, dir, M, st);
+  });
+}
+
+extern "C" int dmrg_sweep(dmrg_ctx* c, int32_t M, dmrg_step_stats* steps, double* energy) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(c->built, DMRG_EINVAL, "dmrg_build_blocks has not been called");
+    int k = 0;
+    dmrg_step_stats st{};
+    for (int p = 1; p <= c->N - 3; ++p) {
+      step(*c, p, 0, M, &st);
+      if (steps) steps[k] = st;
+      ++k;
+    }
+    for (int p = c->N - 3; p >= 1; --p) {
+      step(*c, p, 1, M, &st);
+      if (steps) steps[k] = st;
+      ++k;
+    }
+    if (energy) *energy = st.energy;
+  });
+}
+
+extern "C" int dmrg_block_sectors(dmrg_ctx* c, int32_t side, int32_t b, int32_t* n, int32_t* qn,
+                                  int32_t* dims) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(b >= 0 && b < c->N && (side == 0 || side == 1), DMRG_EINVAL, "bad block");
+    const Blk& B = side == 0 ? c->left[b] : c->right[b];
+    DMRG_REQUIRE(B.valid, DMRG_EINVAL, "block not available");
+    const SectorSet& s = B.ops.sec;
+    if (n) *n = s.size();
+    for (int i = 0; i < s.size(); ++i) {
+      if (qn) {
+        qn[3 * i] = s.q[i].a;
+        qn[3 * i + 1] = s.q[i].b;
+        qn[3 * i + 2] = s.q[i].m;
+      }
+      if (dims) dims[i] = s.d[i];
+    }
+  });
+}
+
+extern "C" int dmrg_heff_cost(dmrg_ctx* c, int32_t p, double* flops, double* bytes,
+                              int64_t* n_items) {
+  return guarded(c, [&] {
+    Super& sb = super_at(*c, p);
+    if (flops) *flops = sb.flops;
+    if (bytes) *bytes = sb.bytes;
+    if (n_items) *n_items = sb.n_items;
+  });
+}
