@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 DMRG hot path.
+
+Workload: pf shell, 40 m-scheme sites, 8 protons + 8 neutrons, M_z = 0 (m-scheme
+dimension 1,087,455,228), J-coupled random two-body ensemble (sigma = 1 MeV, seed 3),
+single-particle energies U[0,4) MeV, M = 4096 block states.  Setup (untimed): starting
+state with M = 4096 per right block, block build, two-site steps from position 1 to the
+middle of the chain.  A timed step is one full two-site DMRG step at the middle of the
+chain (superblock operators, Davidson with H_eff products, reduced-density-matrix
+truncation, renormalization of every normal and complementary operator) in the mixed
+path (FP32 operator contractions, FP64 Davidson / eigensolver / energy).
+
+Reported: value = H_eff psi TFLOP/s over the timed steps (algorithmic flops of every
+H_eff product / wall time of the steps), the H_eff products' own device time and their
+HBM roofline, seconds per sweep at M = 4096, the FP64 path on the same step and the
+energy difference between the two, and the FP64 CPU oracle as the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_eff·ψ TFLOP/s + sweep s at M=4096, mixed vs FP64 GPU at |ΔE|≤1e-5 MeV"
+WORKLOAD = dict(space="pf", Np=8, Nn=8, two_Mz=0, seed=3, mps_seed=3003, M=4096)
+WORKLOAD_NAME = ("pf-shell 40 sites, 8p+8n, M_z=0 (m-scheme dim 1,087,455,228), random "
+                 "J-coupled TBME sigma=1 MeV seed 3, M=4096, mid-chain two-site steps")
+CPU_SAMPLE = dict(space="sd", Np=2, Nn=2, two_Mz=0, seed=1, mps_seed=5, M=64)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = str(gpu_index)
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9 and parts[0] == self.idx:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _positions(N, start, count):
+    """(p, dir) of a sweep starting at `start` left to right, then back."""
+    seq = [(p, 0) for p in range(1, N - 2)] + [(p, 1) for p in range(N - 3, 0, -1)]
+    i = [x for x, (p, d) in enumerate(seq) if p == start and d == 0][0]
+    out = []
+    while len(out) < count:
+        out.append(seq[i % len(seq)])
+        i += 1
+    return seq[:[x for x, (p, d) in enumerate(seq) if p == start and d == 0][0]], out
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle sample (FP64, numpy, one thread): H_eff products inside two-site steps
+# ------------------------------------------------------------------------------------
+def _oracle_heff_flops(sb):
+    idx = sb.layout.index()
+    f = 0.0
+    for Lk, Rk in zip(sb.L.ops, sb.R.ops):
+        for (QLo, QLi), Lb in Lk.items():
+            if QLi not in idx or QLo not in idx:
+                continue
+            _, QRi, dLi, dRi, _ = idx[QLi]
+            _, QRo, dLo, dRo, _ = idx[QLo]
+            if (QRo, QRi) not in Rk:
+                continue
+            f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo
+            f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo
+            f += min(f1, f2)
+    return f
+
+
+def cpu_oracle_sample(steps, warmup, budget_s=25.0):
+    """Times the oracle's H_eff products during two-site steps of the sd 2p+2n, M=64
+    workload (FP64 numpy).  Returns (TFLOP/s, seconds, products, description)."""
+    from gen import make_problem, initial_mps
+    from oracle.dmrg import OracleDMRG
+    w = CPU_SAMPLE
+    prob = make_problem(w["space"], w["Np"], w["Nn"], w["two_Mz"], seed=w["seed"])
+    o = OracleDMRG(prob, initial_mps(prob, w["M"], w["mps_seed"]))
+    # instrument the oracle's superblock product (timing only; arithmetic untouched)
+    stats = {"flops": 0.0, "t": 0.0, "n": 0}
+    orig = o.superblock
+
+    def timed_superblock(p):
+        sb = orig(p)
+        fl = _oracle_heff_flops(sb)
+        app = sb.apply
+
+        def apply(x):
+            t0 = time.perf_counter()
+            y = app(x)
+            stats["t"] += time.perf_counter() - t0
+            stats["flops"] += fl
+            stats["n"] += 1
+            return y
+        sb.apply = apply
+        return sb
+    o.superblock = timed_superblock
+    N = prob.n_sites
+    mid = N // 2 - 1
+    t_start = time.perf_counter()
+    for p in range(1, mid):
+        o.run_step(p, "L", w["M"])
+    stats.update(flops=0.0, t=0.0, n=0)
+    done = 0
+    for p in range(mid, N - 2):
+        if done >= warmup + steps or time.perf_counter() - t_start > budget_s:
+            break
+        if done == warmup:
+            stats.update(flops=0.0, t=0.0, n=0)
+        o.run_step(p, "L", w["M"])
+        done += 1
+    tf = stats["flops"] / max(stats["t"], 1e-12) / 1e12
+    desc = (f"oracle H_eff products in {max(done - warmup, 0)} mid-chain two-site steps of sd "
+            f"2p+2n (m-scheme dim 640), M=64, FP64 numpy; {stats['n']} products, "
+            f"{stats['t']:.2f} s (the pf 8p+8n environment takes the plain oracle ~200 s to "
+            f"build)")
+    return tf, stats["t"], stats["n"], desc
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    t0 = time.perf_counter()
+    tf, secs, nprod, desc = cpu_oracle_sample(args.steps, args.warmup, budget_s=240.0)
+    line = {"impl": "reference", "metric": METRIC, "value": tf, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": desc},
+            "cpu_baseline": {"value": tf, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": tf, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _cpu_baseline_subprocess(steps, warmup):
+    """The oracle sample in a child process pinned to one BLAS thread."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_oracle_sample(%d, %d)))" % (ROOT, steps, warmup))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        return None
+    tf, secs, nprod, desc = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": tf, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": desc,
+            "host_cores": os.cpu_count()}
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_1507_00161_gb300.build import build
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    import paper_1507_00161_gb300 as P
+    from gen import make_problem, initial_mps
+    w = WORKLOAD
+    M = args.M
+    prob = make_problem(w["space"], w["Np"], w["Nn"], w["two_Mz"], seed=w["seed"])
+    init = initial_mps(prob, M, w["mps_seed"])
+    d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
+    d.build_blocks(init)
+    N = prob.n_sites
+    start = N // 2 - 1 - args.warmup
+    setup, seq = _positions(N, max(start, 1), args.warmup + args.steps)
+    for (p, dr) in setup:
+        d.step(p, dr, M)
+    for (p, dr) in seq[:args.warmup]:
+        d.step(p, dr, M)
+    timed = seq[args.warmup:]
+    torch.cuda.synchronize()
+    c0 = d.counters()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed) + 1)]
+    stats = []
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if args.profile_range:
+            torch.cuda.profiler.start()
+        ev[0].record()
+        for i, (p, dr) in enumerate(timed):
+            stats.append(d.step(p, dr, M))
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        if args.profile_range:
+            torch.cuda.profiler.stop()
+        if dist:
+            dist.barrier()
+    c1 = d.counters()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(timed))]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    flops = sum(s["heff_flops"] * s["n_products"] for s in stats)
+    heff_s = sum(s["heff_seconds"] for s in stats)
+    heff_bytes = sum(s["heff_bytes"] * s["n_products"] for s in stats)
+    nprod = sum(s["n_products"] for s in stats)
+    value = world * flops / total_s / 1e12
+    peak, peak_kind = _peaks()
+    achieved = heff_bytes / max(heff_s, 1e-12) / 1e9
+    # end to end through the public API with host buffers: H_eff products at the next
+    # position, psi copied host->device and the result device->host every product
+    p_e2e, _ = seq[-1]
+    lay = d.psi_layout(p_e2e)
+    f_e2e, b_e2e, _ = d.heff_cost(p_e2e)
+    xh = torch.randn(lay["size"], dtype=torch.float64).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty(lay["size"], dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        d.heff_apply(p_e2e, xd, yd)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 3)
+    e0.record()
+    for _ in range(reps):
+        xd.copy_(xh, non_blocking=True)
+        d.heff_apply(p_e2e, xd, yd)
+        yh.copy_(yd, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3 / reps
+    # FP64 path on the same superblock: Davidson from the mixed eigenvector
+    psi_m = torch.empty(lay["size"], dtype=torch.float64, device="cuda")
+    e_mixed, st_m = d.davidson(p_e2e, out=psi_m, allow_noconv=True)
+    d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
+    c2 = d.counters()
+    e_fp64, st_d = d.davidson(p_e2e, guess=psi_m, allow_noconv=True)
+    c3 = d.counters()
+    fp64_tf = (c3["heff_flops"] - c2["heff_flops"]) / max(c3["heff_seconds"] - c2["heff_seconds"],
+                                                           1e-12) / 1e12
+    d.set_options(precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
+    # one full sweep at M = 4096 in the mixed path
+    sweep_s = None
+    if args.sweep:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sw_steps, _ = d.sweep(M)
+        torch.cuda.synchronize()
+        sweep_s = time.perf_counter() - t0
+    clocks = clk.summary()
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = _cpu_baseline_subprocess(args.steps, args.warmup)
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "M": M, "positions": timed,
+                   "precision": "FP32 contractions, FP64 Davidson/eigensolver/energy",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2: %.0f MB of operator blocks per H_eff product"
+                         % (heff_bytes / max(nprod, 1) / 1e6)},
+        "heff": {"tflops_device": flops / max(heff_s, 1e-12) / 1e12, "products": nprod,
+                 "device_s": heff_s, "flops_per_product": flops / max(nprod, 1),
+                 "bytes_per_product": heff_bytes / max(nprod, 1)},
+        "sweep_s": sweep_s,
+        "fp64": {"heff_tflops": fp64_tf, "energy": e_fp64, "products": st_d["n_products"],
+                 "energy_mixed": e_mixed, "dE_mixed_vs_fp64": abs(e_mixed - e_fp64)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "H_eff product (task-list GEMM stages)",
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": f_e2e / e2e_s / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": int(lay["size"]) * 8,
+                "d2h_bytes_per_step": int(lay["size"]) * 8},
+        "gpu_launches": int(c1["launches"] - c0["launches"]),
+        "clocks": clocks,
+        "energies": [s["energy"] for s in stats],
+        "step_ms": step_ms,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--M", type=int, default=WORKLOAD["M"])
+    ap.add_argument("--max-iter", type=int, default=100)
+    ap.add_argument("--sweep", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

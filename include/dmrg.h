@@ -98,7 +98,21 @@ typedef struct {
   int32_t p, dir;           /* position and direction (0 = left to right, 1 = back)    */
   int32_t n_products, kept;
   double energy, residual, trunc_err, seconds;
+  double heff_seconds;      /* device time of the H_eff products (CUDA events)         */
+  double heff_flops;        /* algorithmic flops of one H_eff product at this position */
+  double heff_bytes;        /* algorithmic bytes of one H_eff product                  */
 } dmrg_step_stats;
+
+/* Cumulative counters of a context since creation: kernel launches issued by the
+ * library, H_eff products, their device time (CUDA events on the context stream) and
+ * algorithmic flops and bytes. */
+typedef struct {
+  int64_t launches;
+  int64_t heff_products;
+  double heff_seconds;
+  double heff_flops;
+  double heff_bytes;
+} dmrg_counters;
 
 /* Create a context for one problem (Eq. 1 and a target state).  Validates the input
  * (permutation, index ranges, i<j and k<l, quantum-number conservation, Hermitian list)
@@ -160,6 +174,15 @@ int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy)
  * side 1 = right block of bond b.  NULL arrays query n. */
 int dmrg_block_sectors(dmrg_ctx* ctx, int32_t side, int32_t b, int32_t* n, int32_t* qn,
                        int32_t* dims);
+
+/* Replace the options of a live context (precision, Davidson tolerances, stream); the
+ * blocks are kept.  In DMRG_MIXED_FP32 the Davidson residual is computed from FP32
+ * products, so the stopping test uses max(dav_tol, 1e-6 |theta|); the reported energy
+ * is the FP64 Rayleigh quotient of the converged vector. */
+int dmrg_set_options(dmrg_ctx* ctx, const dmrg_options* opt);
+
+/* Read the cumulative counters. */
+int dmrg_get_counters(dmrg_ctx* ctx, dmrg_counters* out);
 
 /* Algorithmic cost of one H_eff product at position p: flops (2 per multiply-add, the
  * cheaper order of the two products of each term) and bytes (operator blocks read once

@@ -25,7 +25,7 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
-            "dmrg_heff_cost"]
+            "dmrg_set_options", "dmrg_get_counters", "dmrg_heff_cost"]
 
 
 class DmrgError(RuntimeError):
@@ -65,10 +65,17 @@ class StepStats(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("dir", ctypes.c_int32), ("n_products", ctypes.c_int32),
                 ("kept", ctypes.c_int32), ("energy", ctypes.c_double),
                 ("residual", ctypes.c_double), ("trunc_err", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("heff_seconds", ctypes.c_double),
+                ("heff_flops", ctypes.c_double), ("heff_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("heff_products", ctypes.c_int64),
+                ("heff_seconds", ctypes.c_double), ("heff_flops", ctypes.c_double),
+                ("heff_bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -97,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "dmrg_sweep": [P, i32, P, P],
         "dmrg_block_sectors": [P, i32, i32, P, P, P],
         "dmrg_heff_cost": [P, i32, P, P, P],
+        "dmrg_set_options": [P, ctypes.POINTER(Options)],
+        "dmrg_get_counters": [P, ctypes.POINTER(Counters)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -142,11 +151,7 @@ class DMRG:
                      k["v_val"].ctypes.data if k["v_val"].size else None,
                      k["order"].ctypes.data, int(problem.Np), int(problem.Nn),
                      int(problem.two_Mz))
-        stream_ptr = None
-        if stream is not None:
-            stream_ptr = stream if isinstance(stream, int) else stream.cuda_stream
-        opt = Options(int(precision), 0, float(dav_tol), int(dav_max_iter), int(dav_max_sub),
-                      stream_ptr)
+        opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream)
         h = ctypes.c_void_p()
         rc = self.lib.dmrg_create(ctypes.byref(pr), ctypes.byref(opt), ctypes.byref(h))
         self.h = h.value
@@ -154,6 +159,24 @@ class DMRG:
             msg = self.lib.dmrg_last_error(self.h).decode() if self.h else "create failed"
             self.close()
             raise DmrgError(rc, msg)
+
+    @staticmethod
+    def _options(precision, dav_tol, dav_max_iter, dav_max_sub, stream):
+        stream_ptr = None
+        if stream is not None:
+            stream_ptr = stream if isinstance(stream, int) else stream.cuda_stream
+        return Options(int(precision), 0, float(dav_tol), int(dav_max_iter), int(dav_max_sub),
+                       stream_ptr)
+
+    def set_options(self, precision=FP64, dav_tol=1e-8, dav_max_iter=100, dav_max_sub=24,
+                    stream=None):
+        opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream)
+        self._check(self.lib.dmrg_set_options(self.h, ctypes.byref(opt)))
+
+    def counters(self):
+        c = Counters()
+        self._check(self.lib.dmrg_get_counters(self.h, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in Counters._fields_}
 
     def close(self):
         if getattr(self, "h", None):

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,8 @@
 #include "../../include/dmrg.h"
 
 namespace dmrg {
+
+extern std::atomic<int64_t> g_launches;
 
 // ---------------------------------------------------------------------------------------
 // errors: every failure inside the library throws Error; the C-ABI turns it into a status
@@ -27,6 +30,13 @@ struct Error : std::runtime_error {
     cudaError_t e_ = (call);                                                              \
     if (e_ != cudaSuccess)                                                                \
       throw ::dmrg::Error(DMRG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// every kernel launch of the library is followed by DMRG_LAUNCHED(): error check + count
+#define DMRG_LAUNCHED()                                 \
+  do {                                                  \
+    DMRG_CUDA(cudaGetLastError());                      \
+    ::dmrg::g_launches.fetch_add(1, std::memory_order_relaxed); \
   } while (0)
 
 #define DMRG_REQUIRE(cond, code, msg)                 \

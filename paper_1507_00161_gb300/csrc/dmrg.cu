@@ -112,6 +112,15 @@ struct dmrg_ctx {
   dmrg::DevBuf<float> f32a, f32b, f32T;
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
+  // H_eff timing: event pairs recorded around every product, resolved after a sync
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  int64_t heff_products = 0;
+  double heff_seconds = 0, heff_flops = 0, heff_bytes = 0;
+  double step_heff_seconds = 0;
+  ~dmrg_ctx() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
 };
 
 namespace dmrg {
@@ -593,6 +602,46 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y) {
   }
 }
 
+// H_eff product with its device time recorded (events resolved by resolve_heff_timing)
+static void heff_timed(Ctx& c, Super& sb, const double* x, double* y) {
+  if (c.ev_used + 2 > int(c.ev.size())) {
+    // resolve what is pending before reusing events
+    DMRG_CUDA(cudaStreamSynchronize(c.stream));
+    for (int i = 0; i + 1 < c.ev_used; i += 2) {
+      float ms = 0;
+      DMRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
+      c.step_heff_seconds += ms * 1e-3;
+    }
+    c.ev_used = 0;
+    while (c.ev.size() < 256) {
+      cudaEvent_t e;
+      DMRG_CUDA(cudaEventCreate(&e));
+      c.ev.push_back(e);
+    }
+  }
+  DMRG_CUDA(cudaEventRecord(c.ev[c.ev_used], c.stream));
+  heff(c, sb, x, y);
+  DMRG_CUDA(cudaEventRecord(c.ev[c.ev_used + 1], c.stream));
+  c.ev_used += 2;
+  c.heff_products += 1;
+  c.heff_flops += sb.flops;
+  c.heff_bytes += sb.bytes;
+}
+
+static double resolve_heff_timing(Ctx& c) {
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  for (int i = 0; i + 1 < c.ev_used; i += 2) {
+    float ms = 0;
+    DMRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
+    c.step_heff_seconds += ms * 1e-3;
+  }
+  c.ev_used = 0;
+  double s = c.step_heff_seconds;
+  c.heff_seconds += s;
+  c.step_heff_seconds = 0;
+  return s;
+}
+
 // FP64 product regardless of the context precision (energy of the mixed path)
 static void heff64(Ctx& c, Super& sb, const double* x, double* y) {
   int keep = c.opt.precision;
@@ -652,6 +701,7 @@ struct DavResult {
   double theta = 0, resid = 0;
   int nprod = 0;
   bool converged = false;
+  double heff_seconds = 0;
 };
 
 static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
@@ -682,7 +732,7 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
   d2d(vec(0), guess);
   dot(vec(0), vec(0), n, sc, part, s);
   scale_vec(vec(0), n, sc, 1, s);
-  heff(c, sb, vec(0), avec(0));
+  heff_timed(c, sb, vec(0), avec(0));
   int nprod = 1, k = 1;
   multidot(Vp, 1, avec(0), n, Hs, part, s);
   DavResult res;
@@ -701,8 +751,11 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
     res.theta = theta;
     res.resid = rn;
     res.nprod = nprod;
-    if (rn <= tol || nprod >= c.opt.dav_max_iter) {
-      res.converged = rn <= tol;
+    // FP32 products cannot resolve residuals below ~1e-7 of |H|: relative floor
+    const double tol_eff =
+        c.opt.precision == DMRG_FP64 ? tol : std::max(tol, 1e-6 * std::max(1.0, std::fabs(theta)));
+    if (rn <= tol_eff || nprod >= c.opt.dav_max_iter) {
+      res.converged = rn <= tol_eff;
       break;
     }
     // correction t = r / (theta - D), clamped
@@ -715,7 +768,7 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
       d2d(avec(0), c.Ax.p);
       d2d(avec(1), c.Ax1.p);
       k_set_hs_diag<<<1, 32, 0, s>>>(Hs, 64, w);
-      DMRG_CUDA(cudaGetLastError());
+      DMRG_LAUNCHED();
       k = 2;
     }
     dot(c.t.p, c.t.p, n, sc + 2, part, s);
@@ -729,7 +782,7 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
     if (tn <= 1e-14 * std::max(tn0, 1e-300)) break;   // no new direction left
     d2d(vec(k), c.t.p);
     scale_vec(vec(k), n, sc + 3, 1, s);
-    heff(c, sb, vec(k), avec(k));
+    heff_timed(c, sb, vec(k), avec(k));
     ++nprod;
     multidot(Vp, k + 1, avec(k), n, Hs + 64 * k, part, s);
     ++k;
@@ -744,7 +797,7 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
     res.theta = h[0];
   }
   d2d(out, c.x.p);
-  DMRG_CUDA(cudaStreamSynchronize(s));
+  res.heff_seconds = resolve_heff_timing(c);
   return res;
 }
 
@@ -1086,6 +1139,7 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   predict(c, sb, p, dir, c.psi_guess.p);
   c.psi.alloc(std::max<int64_t>(sb.size, 1));
   DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p);
+  const double flops = sb.flops, bytes = sb.bytes;
   c.psi_valid = true;
   c.psi_p = p;
   TruncResult tr = truncate_renormalize(c, p, dir, M);
@@ -1098,6 +1152,9 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
     st->residual = r.resid;
     st->trunc_err = tr.trunc;
     st->seconds = now_s() - t0;
+    st->heff_seconds = r.heff_seconds;
+    st->heff_flops = flops;
+    st->heff_bytes = bytes;
   }
 }
 
@@ -1308,6 +1365,37 @@ extern "C" int dmrg_block_sectors(dmrg_ctx* c, int32_t side, int32_t b, int32_t*
       }
       if (dims) dims[i] = s.d[i];
     }
+  });
+}
+
+extern "C" int dmrg_set_options(dmrg_ctx* c, const dmrg_options* opt) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(opt != nullptr, DMRG_EINVAL, "options are NULL");
+    DMRG_REQUIRE(opt->precision == DMRG_FP64 || opt->precision == DMRG_MIXED_FP32, DMRG_EINVAL,
+                 "unknown precision");
+    DMRG_REQUIRE(opt->dav_tol > 0 && opt->dav_max_iter >= 1 && opt->dav_max_sub >= 4 &&
+                     opt->dav_max_sub <= 64,
+                 DMRG_EINVAL, "bad Davidson options");
+    const bool prec_changed = opt->precision != c->opt.precision;
+    c->opt = *opt;
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+    if (prec_changed && c->sb) {
+      // byte counts and FP32 operator shadows depend on the precision
+      int p = c->sb->p;
+      c->sb.reset();
+      (void)p;
+    }
+  });
+}
+
+extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(out != nullptr, DMRG_EINVAL, "NULL output");
+    out->launches = g_launches.load();
+    out->heff_products = c->heff_products;
+    out->heff_seconds = c->heff_seconds;
+    out->heff_flops = c->heff_flops;
+    out->heff_bytes = c->heff_bytes;
   });
 }
 

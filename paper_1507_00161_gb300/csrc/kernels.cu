@@ -12,9 +12,13 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "common.h"
 
 namespace dmrg {
+
+std::atomic<int64_t> g_launches{0};
 
 constexpr int kWarp = 32;
 
@@ -187,12 +191,12 @@ void run_gemm_tasks(const DevTaskList& L, const Bases<T>& b, int beta_zero, cuda
     int64_t threads = L.n_small * kWarp;
     int blocks = int((threads + 255) / 256);
     k_gemm_small<T><<<blocks, 256, 0, s>>>(L.small_tasks.p, L.n_small, L.terms.p, b, beta_zero);
-    DMRG_CUDA(cudaGetLastError());
+    DMRG_LAUNCHED();
   }
   if (L.n_tiles) {
     k_gemm_tiled<T><<<int(L.n_tiles), 256, 0, s>>>(L.tiles.p, L.large_tasks.p, L.terms.p, b,
                                                    beta_zero);
-    DMRG_CUDA(cudaGetLastError());
+    DMRG_LAUNCHED();
   }
 }
 template void run_gemm_tasks<double>(const DevTaskList&, const Bases<double>&, int, cudaStream_t);
@@ -227,7 +231,7 @@ void run_copy_tasks(const CopyTask* d_tasks, int64_t n_tasks, const CopyTerm* d_
   if (!n_tasks) return;
   int blocks = int((n_tasks * kWarp + 255) / 256);
   k_copy<T><<<blocks, 256, 0, s>>>(d_tasks, n_tasks, d_terms, b);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 template void run_copy_tasks<double>(const CopyTask*, int64_t, const CopyTerm*,
                                      const Bases<double>&, cudaStream_t);
@@ -282,7 +286,7 @@ void multidot(const double* const* d_vecs, int k, const double* w, int64_t n, do
   if (k <= 0) return;
   k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(d_vecs, k, w, n, d_partials);
   k_multidot_final<<<k, 256, 0, s>>>(d_partials, k, kDotBlocks, d_out);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 __global__ void k_lincomb(const double* const* vecs, const double* __restrict__ coef, int k,
@@ -300,7 +304,7 @@ void lincomb(const double* const* d_vecs, const double* d_coef, int k, int64_t n
   int blocks = int(std::min<int64_t>((n + 255) / 256, 152 * 16));
   if (blocks < 1) blocks = 1;
   k_lincomb<<<blocks, 256, 0, s>>>(d_vecs, d_coef, k, n, out, beta_out, coef_scale);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 __global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
@@ -318,7 +322,7 @@ void dot(const double* a, const double* b, int64_t n, double* d_out, double* d_p
          cudaStream_t s) {
   k_dot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, n, d_partials);
   k_multidot_final<<<1, 256, 0, s>>>(d_partials, 1, kDotBlocks, d_out);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 __global__ void k_residual(const double* __restrict__ x, const double* __restrict__ Ax,
@@ -333,7 +337,7 @@ void davidson_residual(const double* x, const double* Ax, const double* d_theta,
                        double* r, cudaStream_t s) {
   int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
   k_residual<<<blocks, 256, 0, s>>>(x, Ax, d_theta, n, r);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 __global__ void k_correction(const double* __restrict__ r, const double* __restrict__ diag,
@@ -351,7 +355,7 @@ void davidson_correction(const double* r, const double* diag, const double* d_th
                          double* t, cudaStream_t s) {
   int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
   k_correction<<<blocks, 256, 0, s>>>(r, diag, d_theta, n, t);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 __global__ void k_scale(double* __restrict__ x, int64_t n, const double* __restrict__ sc,
@@ -366,7 +370,7 @@ __global__ void k_scale(double* __restrict__ x, int64_t n, const double* __restr
 void scale_vec(double* x, int64_t n, const double* d_scale, int invert_sqrt, cudaStream_t s) {
   int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
   k_scale<<<blocks, 256, 0, s>>>(x, n, d_scale, invert_sqrt);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 __global__ void k_fill(double* __restrict__ x, int64_t n, double v) {
@@ -379,7 +383,7 @@ void fill_value(double* x, int64_t n, double v, cudaStream_t s) {
   if (n <= 0) return;
   int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
   k_fill<<<blocks, 256, 0, s>>>(x, n, v);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // ------------------------------------------------------------------------------------
@@ -407,7 +411,7 @@ void heff_diag(const DiagTask* d_tasks, int n_tasks, const DiagTerm* d_terms,
                const double* lops, const double* rops, double* out, cudaStream_t s) {
   if (!n_tasks) return;
   k_heff_diag<<<n_tasks, 128, 0, s>>>(d_tasks, n_tasks, d_terms, lops, rops, out);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // ------------------------------------------------------------------------------------
@@ -555,7 +559,7 @@ void batched_eigh2(const int64_t* d_off, const int64_t* d_woff, const int32_t* d
                    cudaStream_t s) {
   if (n <= 0) return;
   k_batched_eigh2<<<n, 256, 0, s>>>(d_off, d_woff, d_dim, d_A, d_V, d_Vs, d_w, descending, clip);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // Ritz problem: H (k x k, leading dimension ld) -> ascending eigenvalues w, eigenvectors Y
@@ -580,7 +584,7 @@ __global__ void k_ritz(const double* __restrict__ H, int ld, int k, double* A, d
 void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w, double* d_Y,
                 cudaStream_t s) {
   k_ritz<<<1, 256, 0, s>>>(d_H, ld, k, d_scratch, d_scratch + 64 * 64, d_w, d_Y);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // ------------------------------------------------------------------------------------
@@ -614,7 +618,7 @@ void kth_largest(const double* w, int64_t n, int64_t k, double* d_scratch, doubl
   int64_t np2 = 1;
   while (np2 < n) np2 <<= 1;
   k_kth_largest<<<1, 1024, 0, s>>>(w, n, k, d_scratch, np2, out);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // kept count and kept weight per sector: w sorted descending inside each sector
@@ -639,7 +643,7 @@ void count_kept(const int64_t* d_woff, const int32_t* d_dim, int nsec, const dou
   if (nsec <= 0) return;
   k_count_kept<<<(nsec + 127) / 128, 128, 0, s>>>(d_woff, d_dim, nsec, w, d_thr, d_kept,
                                                   d_kept_weight);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // U (D x m, row-major) = first m columns of the sorted, sign-fixed eigenvectors Vs (D x D)
@@ -660,7 +664,7 @@ void gather_u(const int64_t* d_voff, const int32_t* d_dim, const int32_t* d_kept
               const int64_t* d_uoff, int nsec, const double* Vs, double* U, cudaStream_t s) {
   if (nsec <= 0) return;
   k_gather_u<<<nsec, 128, 0, s>>>(d_voff, d_dim, d_kept, d_uoff, Vs, U);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 // FP64 -> FP32 conversion (operator shadows of the mixed-precision path)
@@ -678,13 +682,13 @@ void to_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)));
   k_to_f32<<<blocks, 256, 0, s>>>(x, y, n);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 void to_f64(const float* x, double* y, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)));
   k_to_f64<<<blocks, 256, 0, s>>>(x, y, n);
-  DMRG_CUDA(cudaGetLastError());
+  DMRG_LAUNCHED();
 }
 
 }  // namespace dmrg
