@@ -175,6 +175,29 @@ int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy)
 int dmrg_block_sectors(dmrg_ctx* ctx, int32_t side, int32_t b, int32_t* n, int32_t* qn,
                        int32_t* dims);
 
+/* H_eff psi for callers that cannot allocate device memory during the call: processes
+ * whose device memory is owned and budgeted up front by another allocator (for example a
+ * serving framework that reserved the GPU), code that must not pay the implicit device
+ * synchronisation of cudaMalloc / cudaFree, or code that cannot recover from a failed
+ * allocation.  The paper has no counterpart; this is a service of the library.
+ *   Result: the same product as dmrg_heff_apply, always with FP64 contractions.  Inputs
+ * and outputs are the caller's device vectors as for dmrg_heff_apply.
+ *   Storage: the intermediate of the two contraction stages lives in one file-scope
+ * device array of 2,097,152 doubles (16 MiB) that every GPU loading the library holds
+ * until the process exits.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  A product that needs more intermediate storage is rejected with DMRG_EINVAL
+ * and a message giving the size it needs.
+ *   Preconditions: the superblock at p must already be set up by an allocating call at
+ * the same position (dmrg_psi_layout or dmrg_heff_apply); otherwise DMRG_EINVAL.
+ *   First call on a device: it looks up the array's device address (once per device,
+ * with that device current; with lazy module loading the driver loads the code that
+ * holds the array at that moment); make that first call before any stream capture.
+ *   Concurrency: all calls share the one array.  Calls whose work overlaps on the GPU
+ * (other streams, other contexts on the same device, other threads) race and corrupt
+ * each other's results; serialise them. */
+int dmrg_heff_apply_noalloc(dmrg_ctx* ctx, int32_t p, const double* psi_in_dev,
+                            double* psi_out_dev);
+
 /* Replace the options of a live context (precision, Davidson tolerances, stream); the
  * blocks are kept.  In DMRG_MIXED_FP32 the Davidson residual is computed from FP32
  * products, so the stopping test uses max(dav_tol, 1e-6 |theta|); the reported energy

@@ -25,7 +25,8 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
-            "dmrg_set_options", "dmrg_get_counters", "dmrg_heff_cost"]
+            "dmrg_set_options", "dmrg_get_counters", "dmrg_heff_cost",
+            "dmrg_heff_apply_noalloc"]
 
 
 class DmrgError(RuntimeError):
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_build_blocks": [P, ctypes.POINTER(MpsInit)],
         "dmrg_psi_layout": [P, i32, P, P, P, P, P, P],
         "dmrg_heff_apply": [P, i32, P, P],
+        "dmrg_heff_apply_noalloc": [P, i32, P, P],
         "dmrg_davidson": [P, i32, P, P, P, ctypes.POINTER(DavStats)],
         "dmrg_truncate_renormalize": [P, i32, i32, i32, P, P],
         "dmrg_step": [P, i32, i32, i32, ctypes.POINTER(StepStats)],
@@ -218,6 +220,11 @@ class DMRG:
 
     def heff_apply(self, p, x, y):
         self._check(self.lib.dmrg_heff_apply(self.h, p, _ptr(x), _ptr(y)))
+
+    def heff_apply_noalloc(self, p, x, y):
+        """H_eff psi through the allocation-free entry point (FP64; the superblock at p
+        must have been set up by psi_layout or heff_apply first)."""
+        self._check(self.lib.dmrg_heff_apply_noalloc(self.h, p, _ptr(x), _ptr(y)))
 
     def davidson(self, p, guess=None, out=None, allow_noconv=False):
         e = ctypes.c_double()

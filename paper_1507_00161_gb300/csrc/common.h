@@ -274,4 +274,18 @@ void gather_u(const int64_t* d_voff, const int32_t* d_dim, const int32_t* d_kept
 void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 void to_f64(const float* x, double* y, int64_t n, cudaStream_t s);
 
+// read-only view of the H_eff task lists of the superblock currently set up at position p
+// (nothing is built or allocated; false if the superblock at p is not set up)
+struct HeffView {
+  const DevTaskList* st1;
+  const DevTaskList* st2;
+  const double* L;
+  const double* R;
+  int64_t size;
+  int64_t t_elems;
+  cudaStream_t stream;
+};
+bool heff_view(dmrg_ctx* c, int p, HeffView* v);
+void set_error(dmrg_ctx* c, const char* msg);
+
 }  // namespace dmrg

@@ -1158,6 +1158,23 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   }
 }
 
+bool heff_view(dmrg_ctx* c, int p, HeffView* v) {
+  if (!c || !c->sb || c->sb->p != p) return false;
+  Super& sb = *c->sb;
+  v->st1 = &sb.st1;
+  v->st2 = &sb.st2;
+  v->L = sb.L.data.p;
+  v->R = sb.R.data.p;
+  v->size = sb.size;
+  v->t_elems = sb.t_elems;
+  v->stream = c->stream;
+  return true;
+}
+
+void set_error(dmrg_ctx* c, const char* msg) {
+  if (c) c->err = msg;
+}
+
 }  // namespace dmrg
 
 // =======================================================================================
