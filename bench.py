@@ -350,6 +350,8 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(lay["size"]) * 8,
                 "d2h_bytes_per_step": int(lay["size"]) * 8},
         "gpu_launches": int(c1["launches"] - c0["launches"]),
+        "phase_s": {k: c1[k] - c0[k] for k in ("t_enlarge", "t_super", "t_davidson",
+                                               "t_truncate", "t_project", "t_predict")},
         "clocks": clocks,
         "energies": [s["energy"] for s in stats],
         "step_ms": step_ms,

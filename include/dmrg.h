@@ -104,14 +104,16 @@ typedef struct {
 } dmrg_step_stats;
 
 /* Cumulative counters of a context since creation: kernel launches issued by the
- * library, H_eff products, their device time (CUDA events on the context stream) and
- * algorithmic flops and bytes. */
+ * library (all contexts of the process), H_eff products, their device time (CUDA events
+ * on the context stream) and algorithmic flops and bytes, and the wall seconds spent in
+ * the phases of the steps (host bookkeeping included). */
 typedef struct {
   int64_t launches;
   int64_t heff_products;
   double heff_seconds;
   double heff_flops;
   double heff_bytes;
+  double t_enlarge, t_super, t_davidson, t_truncate, t_project, t_predict;
 } dmrg_counters;
 
 /* Create a context for one problem (Eq. 1 and a target state).  Validates the input

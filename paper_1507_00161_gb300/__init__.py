@@ -76,7 +76,10 @@ class StepStats(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("heff_products", ctypes.c_int64),
                 ("heff_seconds", ctypes.c_double), ("heff_flops", ctypes.c_double),
-                ("heff_bytes", ctypes.c_double)]
+                ("heff_bytes", ctypes.c_double), ("t_enlarge", ctypes.c_double),
+                ("t_super", ctypes.c_double), ("t_davidson", ctypes.c_double),
+                ("t_truncate", ctypes.c_double), ("t_project", ctypes.c_double),
+                ("t_predict", ctypes.c_double)]
 
 
 _lib = None

@@ -79,23 +79,91 @@ struct SectorSet {
 };
 
 // ---------------------------------------------------------------------------------------
-// device memory
+// device memory: a per-context caching pool.  All device work of a context runs on its one
+// stream, so a block returned to the pool may be handed out again at once (stream order
+// keeps the earlier users ahead).  Blocks are kept in power-of-two classes and released
+// with cudaFree only when the context is destroyed (or a cudaMalloc fails).
 // ---------------------------------------------------------------------------------------
+struct Pool {
+  std::vector<std::pair<size_t, void*>> free_blocks;   // (class bytes, pointer)
+  size_t cached = 0;
+  ~Pool() { trim(); }
+  void trim() {
+    for (auto& b : free_blocks) cudaFree(b.second);
+    free_blocks.clear();
+    cached = 0;
+  }
+  static size_t cls(size_t bytes) {
+    size_t c = 256;
+    while (c < bytes) c <<= 1;
+    return c;
+  }
+  void* get(size_t bytes, size_t* got) {
+    const size_t c = cls(bytes);
+    for (size_t i = free_blocks.size(); i-- > 0;)
+      if (free_blocks[i].first == c) {
+        void* p = free_blocks[i].second;
+        free_blocks[i] = free_blocks.back();
+        free_blocks.pop_back();
+        cached -= c;
+        *got = c;
+        return p;
+      }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, c);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      trim();
+      e = cudaMalloc(&p, c);
+    }
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw Error(DMRG_ENOMEM, "cudaMalloc of " + std::to_string(c) + " bytes failed");
+    }
+    *got = c;
+    return p;
+  }
+  void put(void* p, size_t c) {
+    free_blocks.push_back({c, p});
+    cached += c;
+  }
+};
+
+// the pool of the context whose C-ABI call is running on this thread (nullptr: plain
+// cudaMalloc / cudaFree)
+extern thread_local Pool* tl_pool;
+
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   int64_t n = 0;
+  size_t cls = 0;
+  Pool* pool = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), cls(o.cls), pool(o.pool) {
+    o.p = nullptr;
+    o.n = 0;
+  }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) {
+      release();
+      p = o.p;
+      n = o.n;
+      cls = o.cls;
+      pool = o.pool;
+      o.p = nullptr;
+      o.n = 0;
+    }
     return *this;
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (pool) pool->put(p, cls);
+      else cudaFree(p);
+    }
     p = nullptr;
     n = 0;
   }
@@ -103,12 +171,22 @@ struct DevBuf {
     if (count <= n && p) return;
     release();
     if (count > 0) {
-      cudaError_t e = cudaMalloc(&p, sizeof(T) * size_t(count));
-      if (e != cudaSuccess) {
-        p = nullptr;
-        throw Error(DMRG_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed");
+      const size_t bytes = sizeof(T) * size_t(count);
+      pool = tl_pool;
+      if (pool) {
+        size_t got = 0;
+        p = static_cast<T*>(pool->get(bytes, &got));
+        cls = got;
+        n = int64_t(got / sizeof(T));
+      } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+          p = nullptr;
+          (void)cudaGetLastError();
+          throw Error(DMRG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+        n = count;
       }
-      n = count;
     }
   }
   void upload(const T* h, int64_t count, cudaStream_t s) {
@@ -273,6 +351,52 @@ void gather_u(const int64_t* d_voff, const int32_t* d_dim, const int32_t* d_kept
               const int64_t* d_uoff, int nsec, const double* Vs, double* U, cudaStream_t s);
 void to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 void to_f64(const float* x, double* y, int64_t n, cudaStream_t s);
+
+// fused H_eff product (heff.cu): one term of an output block ...
+struct HeffItem {
+  int64_t loff, roff, xoff;   // L block (dLo x dLi), R block (dRo x dRi), psi_in block (dLi x dRi)
+  int32_t dLi, dRi;
+  float sign;                 // (-1)^{|R_k| N(Q_L)}
+  int32_t pad;
+};
+// ... one unit of work: a group of terms of one output tile (rows r0..r0+m, columns
+// c0..c0+n of the psi' block at yoff); written to psi' directly (poff < 0) or as a partial
+// tile at poff of the scratch, summed later in group order
+struct HeffTile {
+  int64_t yoff;
+  int64_t poff;
+  int32_t ld;                 // dRo of the output block
+  int32_t r0, c0, m, n;
+  int32_t i0, i1;             // items [i0, i1)
+  int32_t pad;
+};
+// deterministic sum of the partial tiles of one output tile
+struct HeffRed {
+  int64_t yoff, poff;
+  int32_t ld, r0, c0, m, n, groups;
+};
+template <class T>
+void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
+                const HeffRed* d_red, int64_t n_red, const T* L, const T* R, const T* X, T* Y,
+                T* partial, cudaStream_t s);
+
+// enlargement of block operators by one site (kernels.cu)
+struct EntryDev {
+  int32_t src;     // source label
+  int32_t op;      // site operator: 0 = 1, 1 = n, 2 = c+, 3 = c
+  double coef;
+};
+struct EnlBlock {
+  int64_t off;     // destination block offset
+  int32_t k, Qo, Qi, pad;
+};
+struct LayDev {
+  int32_t pblk0, pblk1, poff1, D;
+};
+void enlarge_blocks(const EnlBlock* blocks, int64_t n, const int32_t* eptr, const EntryDev* ents,
+                    const int32_t* src_by_in, int src_nsec, const int64_t* src_boff,
+                    const int32_t* src_dim, const int32_t* src_npart, const int8_t* src_lpar,
+                    const LayDev* lay, int left, const double* src, double* out, cudaStream_t s);
 
 // read-only view of the H_eff task lists of the superblock currently set up at position p
 // (nothing is built or allocated; false if the superblock at p is not set up)

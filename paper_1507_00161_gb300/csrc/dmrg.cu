@@ -11,6 +11,7 @@
 #include <cmath>
 #include <memory>
 #include <set>
+#include <thread>
 
 #include "common.h"
 #include "problem.h"
@@ -34,7 +35,12 @@ struct OpSet {
   DevBuf<float> data32;
   int64_t n_elems = 0;
   std::vector<int32_t> by_in;     // nlab x nsec: block index by input sector (or -1)
+  // device copies used when this set is the source of an enlargement
+  DevBuf<int32_t> d_by_in, d_dim, d_npart;
+  DevBuf<int64_t> d_boff;
+  bool dev_index_ready = false;
   void index_by_in() {
+    dev_index_ready = false;
     by_in.assign(size_t(nlab) * sec.size(), -1);
     for (int k = 0; k < nlab; ++k)
       for (int64_t x = lab_ptr[k]; x < lab_ptr[k + 1]; ++x)
@@ -47,6 +53,40 @@ struct Layout {
   SectorSet sec;
   std::vector<std::array<int, 2>> pblk;   // block sector of piece sigma (or -1)
   std::vector<std::array<int, 2>> poff;   // row offset of piece sigma
+};
+
+// O(1) sector lookup over the bounding box of a sector list
+struct QIndex {
+  int a0 = 0, b0 = 0, m0 = 0, na = 0, nb = 0, nm = 0;
+  std::vector<int32_t> idx;
+  explicit QIndex(const SectorSet& s) {
+    if (s.q.empty()) return;
+    int a1 = s.q[0].a, b1 = s.q[0].b, m1 = s.q[0].m;
+    a0 = a1, b0 = b1, m0 = m1;
+    for (auto& q : s.q) {
+      a0 = std::min(a0, q.a), a1 = std::max(a1, q.a);
+      b0 = std::min(b0, q.b), b1 = std::max(b1, q.b);
+      m0 = std::min(m0, q.m), m1 = std::max(m1, q.m);
+    }
+    na = a1 - a0 + 1, nb = b1 - b0 + 1, nm = m1 - m0 + 1;
+    idx.assign(size_t(na) * nb * nm, -1);
+    for (int i = 0; i < s.size(); ++i)
+      idx[(size_t(s.q[i].a - a0) * nb + (s.q[i].b - b0)) * nm + (s.q[i].m - m0)] = i;
+  }
+  int find(const QN& q) const {
+    const int a = q.a - a0, b = q.b - b0, m = q.m - m0;
+    if (a < 0 || a >= na || b < 0 || b >= nb || m < 0 || m >= nm) return -1;
+    return idx[(size_t(a) * nb + b) * nm + m];
+  }
+};
+
+// constant W entries of one site grouped by destination label
+struct SiteEntries {
+  std::vector<int32_t> ptr;
+  std::vector<EntryDev> e;
+  DevBuf<int32_t> dptr;
+  DevBuf<EntryDev> de;
+  bool ready = false;
 };
 
 // basis of a stored block: kept columns of an isometry per enlarged sector
@@ -75,6 +115,17 @@ struct Super {
   std::vector<int> psi_of_L, psi_of_R;
   int64_t size = 0;
   DevTaskList st1, st2;
+  bool two_stage_ready = false;
+  struct Term {
+    int64_t lb, rb;
+    int bin, bout;
+    double sign;
+  };
+  std::vector<Term> terms_host;
+  DevBuf<HeffItem> fitems;
+  DevBuf<HeffTile> ftiles;
+  DevBuf<HeffRed> fred;
+  int64_t n_ftiles = 0, n_fred = 0, p_elems = 0;
   int64_t t_elems = 0;
   double flops = 0, bytes = 0;
   int64_t n_items = 0;
@@ -88,7 +139,11 @@ struct Super {
 }  // namespace dmrg
 
 struct dmrg_ctx {
+  dmrg::Pool pool;   // first member: destroyed last, after every buffer returned to it
   std::string err = "no error";
+  // wall seconds spent in the phases of a step (host bookkeeping + device work)
+  double t_enlarge = 0, t_super = 0, t_davidson = 0, t_truncate = 0, t_project = 0,
+         t_predict = 0;
   dmrg::Chain chain;
   dmrg::MPO mpo;
   dmrg_options opt{};
@@ -109,9 +164,11 @@ struct dmrg_ctx {
   std::unique_ptr<dmrg::Super> prev;   // layouts of the superblock psi belongs to
   // scratch
   dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
-  dmrg::DevBuf<float> f32a, f32b, f32T;
+  dmrg::DevBuf<float> f32a, f32b, f32T, part32;
+  dmrg::DevBuf<double> part64;
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
+  std::vector<dmrg::SiteEntries> ent_left, ent_right;
   // H_eff timing: event pairs recorded around every product, resolved after a sync
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
@@ -125,7 +182,19 @@ struct dmrg_ctx {
 
 namespace dmrg {
 
+thread_local Pool* tl_pool = nullptr;
+
 using Ctx = dmrg_ctx;
+
+static double wall() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+struct PhaseTimer {
+  double& acc;
+  double t0;
+  explicit PhaseTimer(double& a) : acc(a), t0(wall()) {}
+  ~PhaseTimer() { acc += wall() - t0; }
+};
 
 static bool reachable(const std::set<std::tuple<int, int, int>>& s, const QN& q) {
   return s.count(std::make_tuple(q.a, q.b, q.m)) > 0;
@@ -194,140 +263,139 @@ static void make_layout(const Ctx& c, const SectorSet& blk, int s, bool left, La
 }
 
 // operators of the enlarged space (see problem.cu for the recursion); the Jordan-Wigner
-// sign is (-1)^{|op| N(q_in)} on the left and (-1)^{sigma_in |O_block|} on the right
-static void enlarge(Ctx& c, const OpSet& blk, int s, bool left, Layout& lay, OpSet& out) {
-  make_layout(c, blk.sec, s, left, lay);
-  const int nE = lay.sec.size();
-  const QN qs = c.chain.q[s];
-  // block sector -> enlarged sector for sigma = 0, 1
-  std::vector<int> e0(blk.sec.size(), -1), e1(blk.sec.size(), -1);
-  for (int i = 0; i < blk.sec.size(); ++i) {
-    e0[i] = lay.sec.find(blk.sec.q[i]);
-    e1[i] = lay.sec.find(blk.sec.q[i] + qs);
-  }
+// sign is (-1)^{|op| N(q_in)} on the left and (-1)^{sigma_in |O_block|} on the right.
+// The host finds which blocks exist (per label, in parallel) and lays them out; the
+// kernel k_enlarge assembles every block on the device.
+static void ensure_site_entries(Ctx& c, int s, bool left) {
+  SiteEntries& se = left ? c.ent_left[s] : c.ent_right[s];
+  if (se.ready) return;
   const auto& W = c.mpo.W[s];
-  const auto& order = left ? c.w_by_b[s] : c.w_by_a[s];
-  const int nlab_out = left ? int(c.mpo.labels[s + 1].size()) : int(c.mpo.labels[s].size());
-  const auto& src_par = left ? c.mpo.parity[s] : c.mpo.parity[s + 1];
-  out.sec = lay.sec;
-  out.nlab = nlab_out;
-  out.lab_ptr.assign(nlab_out + 1, 0);
-  out.blocks.clear();
-  std::vector<int32_t> blk_of(size_t(nlab_out) * nE, -1);
-  std::vector<std::array<int32_t, 4>> task_of;   // per out block: task per (so, si)
-  std::vector<int32_t> tcount;
-  std::vector<CopyTask> tasks;
-  // pass 1: blocks, tasks, term counts
-  auto visit = [&](auto&& fn) {
-    for (int ei : order) {
-      const WEntry& e = W[ei];
-      const int srcl = left ? e.a : e.b, dstl = left ? e.b : e.a;
-      for (int x = 0; x < 2; ++x) {
-        const int so = kOpEntries[e.op][x][0], si = kOpEntries[e.op][x][1];
-        if (so < 0) continue;
-        for (int64_t bi = blk.lab_ptr[srcl]; bi < blk.lab_ptr[srcl + 1]; ++bi) {
-          const OpBlock& ob = blk.blocks[bi];
-          const int Qi = si ? e1[ob.si] : e0[ob.si];
-          const int Qo = so ? e1[ob.so] : e0[ob.so];
-          if (Qi < 0 || Qo < 0) continue;
-          double sign = 1.0;
-          if (left) {
-            if ((e.op == OP_CD || e.op == OP_C) && (particles(blk.sec.q[ob.si]) & 1)) sign = -1.0;
-          } else {
-            if (si && src_par[srcl]) sign = -1.0;
+  const int ndst = left ? int(c.mpo.labels[s + 1].size()) : int(c.mpo.labels[s].size());
+  se.ptr.assign(ndst + 1, 0);
+  for (const auto& e : W) se.ptr[(left ? e.b : e.a) + 1]++;
+  for (int k = 0; k < ndst; ++k) se.ptr[k + 1] += se.ptr[k];
+  se.e.resize(W.size());
+  std::vector<int32_t> pos(se.ptr.begin(), se.ptr.end() - 1);
+  for (const auto& e : W) {   // W order inside each destination label
+    EntryDev x;
+    x.src = left ? e.a : e.b;
+    x.op = e.op;
+    x.coef = e.coef;
+    se.e[pos[left ? e.b : e.a]++] = x;
+  }
+  se.dptr.upload(se.ptr, c.stream);
+  se.de.upload(se.e, c.stream);
+  se.ready = true;
+}
+
+static void ensure_dev_index(Ctx& c, OpSet& o) {
+  if (o.dev_index_ready) return;
+  std::vector<int64_t> boff(o.blocks.size());
+  for (size_t i = 0; i < o.blocks.size(); ++i) boff[i] = o.blocks[i].off;
+  std::vector<int32_t> dim(o.sec.size()), npart(o.sec.size());
+  for (int i = 0; i < o.sec.size(); ++i) {
+    dim[i] = o.sec.d[i];
+    npart[i] = particles(o.sec.q[i]);
+  }
+  o.d_by_in.upload(o.by_in, c.stream);
+  o.d_boff.upload(boff, c.stream);
+  o.d_dim.upload(dim, c.stream);
+  o.d_npart.upload(npart, c.stream);
+  o.dev_index_ready = true;
+}
+
+template <class F>
+static void parallel_for(int n, F&& fn) {
+  int nt = int(std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency())));
+  if (n < 64 || nt <= 1) {
+    fn(0, n, 0);
+    return;
+  }
+  nt = std::min(nt, n / 16);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int a = int(int64_t(n) * t / nt), b = int(int64_t(n) * (t + 1) / nt);
+    th.emplace_back([&fn, a, b, t] { fn(a, b, t); });
+  }
+  for (auto& x : th) x.join();
+}
+
+static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& out) {
+  PhaseTimer tm(c.t_enlarge);
+  make_layout(c, blk.sec, s, left, lay);
+  ensure_site_entries(c, s, left);
+  ensure_dev_index(c, blk);
+  const SiteEntries& se = left ? c.ent_left[s] : c.ent_right[s];
+  const int nE = lay.sec.size();
+  const int nsrc = blk.sec.size();
+  const int ndst = int(se.ptr.size()) - 1;
+  const auto& dq = left ? c.mpo.dq[s + 1] : c.mpo.dq[s];
+  // destination blocks (label k, Q_in) that receive at least one contribution
+  QIndex qi_index(lay.sec);
+  std::vector<std::vector<EnlBlock>> part(16);
+  std::vector<std::vector<int32_t>> part_lab(16);
+  parallel_for(ndst, [&](int k0, int k1, int t) {
+    auto& v = part[t];
+    for (int k = k0; k < k1; ++k) {
+      // for the right side the operator's quantum-number change is minus that of the label
+      const QN d = left ? dq[k] : QN{0, 0, 0} - dq[k];
+      for (int Qi = 0; Qi < nE; ++Qi) {
+        const int Qo = qi_index.find(lay.sec.q[Qi] + d);
+        if (Qo < 0) continue;
+        bool exists = false;
+        for (int x = se.ptr[k]; x < se.ptr[k + 1] && !exists; ++x) {
+          const EntryDev& e = se.e[x];
+          for (int y = 0; y < 2 && !exists; ++y) {
+            const int so = kOpEntries[e.op][y][0], si = kOpEntries[e.op][y][1];
+            if (so < 0) continue;
+            const int qo = lay.pblk[Qo][so], qi = lay.pblk[Qi][si];
+            if (qo < 0 || qi < 0) continue;
+            if (blk.by_in[size_t(e.src) * nsrc + qi] >= 0) exists = true;
           }
-          fn(dstl, Qo, Qi, so, si, ob, e.coef * sign);
         }
+        if (exists) v.push_back(EnlBlock{0, k, Qo, Qi, 0});
       }
     }
-  };
-  int cur_label = -1;
-  visit([&](int dstl, int Qo, int Qi, int so, int si, const OpBlock& ob, double) {
-    (void)ob;
-    if (dstl != cur_label) {
-      DMRG_REQUIRE(dstl > cur_label, DMRG_EINVAL, "internal: entries not grouped by label");
-      for (int l = cur_label + 1; l <= dstl; ++l) out.lab_ptr[l] = int64_t(out.blocks.size());
-      cur_label = dstl;
-    }
-    int32_t& bid = blk_of[size_t(dstl) * nE + Qi];
-    if (bid < 0) {
-      bid = int32_t(out.blocks.size());
-      out.blocks.push_back(OpBlock{Qo, Qi, 0});
-      task_of.push_back({-1, -1, -1, -1});
-    }
-    int32_t& tid = task_of[bid][so * 2 + si];
-    if (tid < 0) {
-      tid = int32_t(tasks.size());
-      CopyTask t;
-      t.dst.base = B_Y;
-      t.dst.off = bid;   // fixed up below
-      t.dst.ld = 0;
-      t.rows = blk.sec.d[lay.pblk[Qo][so]];
-      t.cols = blk.sec.d[lay.pblk[Qi][si]];
-      t.t0 = so * 2 + si;   // piece code, fixed up below
-      t.t1 = 0;
-      tasks.push_back(t);
-      tcount.push_back(0);
-    }
-    tcount[tid]++;
   });
-  for (int l = cur_label + 1; l <= nlab_out; ++l) out.lab_ptr[l] = int64_t(out.blocks.size());
+  out.sec = lay.sec;
+  out.nlab = ndst;
+  out.lab_ptr.assign(ndst + 1, 0);
+  out.blocks.clear();
+  std::vector<EnlBlock> eb;
+  for (auto& v : part)
+    for (auto& b : v) eb.push_back(b);   // label order: threads own increasing label ranges
   int64_t off = 0;
-  for (auto& b : out.blocks) {
+  for (auto& b : eb) {
+    // 16-byte aligned block offsets (vector loads of the fused product), padded arena
+    off = (off + 3) & ~int64_t(3);
     b.off = off;
-    off += int64_t(lay.sec.d[b.so]) * lay.sec.d[b.si];
+    out.blocks.push_back(OpBlock{b.Qo, b.Qi, off});
+    out.lab_ptr[b.k + 1]++;
+    off += int64_t(lay.sec.d[b.Qo]) * lay.sec.d[b.Qi];
   }
+  for (int k = 0; k < ndst; ++k) out.lab_ptr[k + 1] += out.lab_ptr[k];
   out.n_elems = off;
-  std::vector<int32_t> tpos(tasks.size());
-  int32_t acc = 0;
-  for (size_t t = 0; t < tasks.size(); ++t) {
-    const OpBlock& b = out.blocks[tasks[t].dst.off];
-    const int so = tasks[t].t0 >> 1, si = tasks[t].t0 & 1;
-    const int Di = lay.sec.d[b.si];
-    tasks[t].dst.off = b.off + int64_t(lay.poff[b.so][so]) * Di + lay.poff[b.si][si];
-    tasks[t].dst.ld = Di;
-    tasks[t].t0 = acc;
-    tpos[t] = acc;
-    acc += tcount[t];
-    tasks[t].t1 = acc;
-  }
-  std::vector<CopyTerm> terms(acc);
-  visit([&](int dstl, int Qo, int Qi, int so, int si, const OpBlock& ob, double scale) {
-    (void)Qo;
-    int32_t bid = blk_of[size_t(dstl) * nE + Qi];
-    int32_t tid = task_of[bid][so * 2 + si];
-    CopyTerm& g = terms[tpos[tid]++];
-    g.src.base = B_X;
-    g.src.off = ob.off;
-    g.src.ld = blk.sec.d[ob.si];
-    g.scale = scale;
-  });
-  out.data.alloc(std::max<int64_t>(out.n_elems, 1));
-  {
-    CopyList chk;
-    chk.tasks = tasks;
-    chk.terms = terms;
-    int64_t be[NBASE] = {0};
-    be[B_X] = blk.data.n;
-    be[B_Y] = out.data.n;
-    validate_copy_tasks(chk, be);
-  }
-  DMRG_CUDA(cudaMemsetAsync(out.data.p, 0, sizeof(double) * std::max<int64_t>(out.n_elems, 1),
-                            c.stream));
-  DevBuf<CopyTask> dt;
-  DevBuf<CopyTerm> dg;
-  dt.upload(tasks, c.stream);
-  dg.upload(terms, c.stream);
-  Bases<double> bb{};
-  bb.p[B_X] = blk.data.p;
-  bb.p[B_Y] = out.data.p;
-  run_copy_tasks<double>(dt.p, int64_t(tasks.size()), dg.p, bb, c.stream);
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));   // task buffers are freed on return
+  out.data.alloc(out.n_elems + 4);
+  // layout table for the device
+  std::vector<LayDev> ld(nE);
+  for (int i = 0; i < nE; ++i) ld[i] = LayDev{lay.pblk[i][0], lay.pblk[i][1], lay.poff[i][1], lay.sec.d[i]};
+  DevBuf<LayDev> dlay;
+  DevBuf<EnlBlock> deb;
+  dlay.upload(ld, c.stream);
+  deb.upload(eb, c.stream);
+  const auto& spar = left ? c.mpo.parity[s] : c.mpo.parity[s + 1];
+  DevBuf<int8_t> dpar;
+  dpar.upload(spar, c.stream);
+  enlarge_blocks(deb.p, int64_t(eb.size()), se.dptr.p, se.de.p, blk.d_by_in.p, nsrc, blk.d_boff.p,
+                 blk.d_dim.p, blk.d_npart.p, dpar.p, dlay.p, left ? 1 : 0, blk.data.p,
+                 out.data.p, c.stream);
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));   // the small tables above are released
   out.index_by_in();
 }
 
 // stored block = kept part of an enlarged operator set: O' = U_o^T O U_i per block
 static void project(Ctx& c, OpSet& E, const Iso& iso, OpSet& out) {
+  PhaseTimer tm(c.t_project);
   if (iso.identity) {
     out = std::move(E);
     out.index_by_in();
@@ -437,6 +505,7 @@ static OpSet vacuum_ops(int nlab, int which, cudaStream_t s) {
 // superblock at position p: enlarged operators, wave-function layout, H_eff task lists
 // ---------------------------------------------------------------------------------------
 static void build_super(Ctx& c, int p) {
+  PhaseTimer tm(c.t_super);
   DMRG_REQUIRE(c.built, DMRG_EINVAL, "dmrg_build_blocks has not been called");
   DMRG_REQUIRE(p >= 1 && p <= c.N - 3, DMRG_EINVAL, "position out of range [1, N-3]");
   DMRG_REQUIRE(c.left[p - 1].valid && c.right[p + 1].valid, DMRG_EINVAL,
@@ -489,21 +558,79 @@ static void build_super(Ctx& c, int p) {
       rused[rb] = 1;
     }
   }
-  TaskList s1, s2;
   int64_t toff = 0;
   double flops = 0;
   int64_t items = 0;
+  // fused product: items grouped by output block, output tiles of at most 32 x 32
+  std::vector<HeffItem> fi;
+  struct TileCost {
+    HeffTile t;
+    double cost;
+  };
+  std::vector<TileCost> ft;
+  std::vector<HeffRed> fr;
+  int64_t pelems = 0;
   for (size_t bo = 0; bo < by_out.size(); ++bo) {
+    {
+      const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
+      const int i0 = int(fi.size());
+      double work = 0;
+      for (const Item& it : by_out[bo]) {
+        const int dLi = sb->bdl[it.bin], dRi = sb->bdr[it.bin];
+        HeffItem h;
+        h.loff = sb->L.blocks[it.lb].off;
+        h.roff = sb->R.blocks[it.rb].off;
+        h.xoff = sb->boff[it.bin];
+        h.dLi = dLi;
+        h.dRi = dRi;
+        h.sign = float(it.sign);
+        h.pad = 0;
+        fi.push_back(h);
+        work += double(dLi) * dRi + double(dLi);
+      }
+      const int i1 = int(fi.size());
+      const int G = 64;   // terms per thread block
+      const int groups = std::max(1, (i1 - i0 + G - 1) / G);
+      for (int r0 = 0; r0 < dLo; r0 += 32)
+        for (int c0 = 0; c0 < dRo; c0 += 32) {
+          HeffTile t;
+          t.yoff = sb->boff[bo];
+          t.ld = dRo;
+          t.r0 = r0;
+          t.c0 = c0;
+          t.m = std::min(32, dLo - r0);
+          t.n = std::min(32, dRo - c0);
+          t.pad = 0;
+          const int64_t mn = int64_t(t.m) * t.n;
+          if (groups > 1) {
+            HeffRed rd;
+            rd.yoff = t.yoff;
+            rd.poff = pelems;
+            rd.ld = t.ld;
+            rd.r0 = r0;
+            rd.c0 = c0;
+            rd.m = t.m;
+            rd.n = t.n;
+            rd.groups = groups;
+            fr.push_back(rd);
+          }
+          for (int g = 0; g < groups; ++g) {
+            t.i0 = i0 + g * G;
+            t.i1 = std::min(i1, t.i0 + G);
+            t.poff = groups > 1 ? pelems + g * mn : -1;
+            ft.push_back(TileCost{t, work * double(t.i1 - t.i0) / std::max(1, i1 - i0) * t.n + 1.0});
+          }
+          if (groups > 1) pelems += groups * mn;
+        }
+    }
     if (by_out[bo].empty()) continue;
     const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
-    s2.begin_task(Operand{sb->boff[bo], B_Y, dRo}, dLo, dRo);
     for (const Item& it : by_out[bo]) {
       const int dLi = sb->bdl[it.bin], dRi = sb->bdr[it.bin];
       const OpBlock& lb = sb->L.blocks[it.lb];
       const OpBlock& rb = sb->R.blocks[it.rb];
-      s1.begin_task(Operand{toff, B_T, dRo}, dLi, dRo);
-      s1.add_term(Operand{sb->boff[it.bin], B_X, dRi}, Operand{rb.off, B_ROPS, dRi}, dRi, 2, 1.0);
-      s2.add_term(Operand{lb.off, B_LOPS, dLi}, Operand{toff, B_T, dRo}, dLi, 0, it.sign);
+      (void)lb;
+      (void)rb;
       toff += int64_t(dLi) * dRo;
       double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;
       double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;
@@ -521,15 +648,39 @@ static void build_super(Ctx& c, int p) {
     if (rused[x]) bytes += double(sb->Rl.sec.d[sb->R.blocks[x].so]) * sb->Rl.sec.d[sb->R.blocks[x].si];
   bytes += 2.0 * double(sb->size);
   sb->bytes = bytes * (c.opt.precision == DMRG_FP64 ? 8.0 : 4.0);
+  // terms grouped by output block, kept on the host for the two-stage lists that only
+  // dmrg_psi_layout / dmrg_heff_apply build (the allocation-free product needs them)
+  for (size_t bo = 0; bo < by_out.size(); ++bo)
+    for (const Item& it : by_out[bo])
+      sb->terms_host.push_back({it.lb, it.rb, it.bin, it.bout, it.sign});
   {
-    int64_t be[NBASE] = {0};
-    be[B_X] = sb->size;
-    be[B_Y] = sb->size;
-    be[B_T] = sb->t_elems;
-    be[B_LOPS] = sb->L.n_elems;
-    be[B_ROPS] = sb->R.n_elems;
-    sb->st1.build(s1, be, c.stream);
-    sb->st2.build(s2, be, c.stream);
+    // heaviest tiles first; validate every access range on the host
+    std::stable_sort(ft.begin(), ft.end(),
+                     [](const TileCost& a, const TileCost& b) { return a.cost > b.cost; });
+    std::vector<HeffTile> tl(ft.size());
+    for (size_t i = 0; i < ft.size(); ++i) {
+      const HeffTile& t = ft[i].t;
+      tl[i] = t;
+      DMRG_REQUIRE(t.yoff + int64_t(t.r0 + t.m - 1) * t.ld + t.c0 + t.n - 1 < sb->size,
+                   DMRG_EINVAL, "internal: fused tile out of range");
+      for (int j = t.i0; j < t.i1; ++j) {
+        const HeffItem& h = fi[j];
+        DMRG_REQUIRE(h.loff + int64_t(t.r0 + t.m) * h.dLi - 1 < sb->L.n_elems &&
+                         h.roff + int64_t(t.c0 + t.n) * h.dRi - 1 < sb->R.n_elems &&
+                         h.xoff + int64_t(h.dLi) * h.dRi - 1 < sb->size,
+                     DMRG_EINVAL, "internal: fused item out of range");
+      }
+    }
+    for (const HeffRed& r : fr)
+      DMRG_REQUIRE(r.poff + int64_t(r.groups) * r.m * r.n <= pelems &&
+                       r.yoff + int64_t(r.r0 + r.m - 1) * r.ld + r.c0 + r.n - 1 < sb->size,
+                   DMRG_EINVAL, "internal: partial tile out of range");
+    sb->fitems.upload(fi, c.stream);
+    sb->ftiles.upload(tl, c.stream);
+    sb->fred.upload(fr, c.stream);
+    sb->n_ftiles = int64_t(tl.size());
+    sb->n_fred = int64_t(fr.size());
+    sb->p_elems = pelems;
   }
   // diagonal tasks: terms that keep the sector (Delta q = 0)
   std::vector<DiagTask> dt;
@@ -558,8 +709,8 @@ static void build_super(Ctx& c, int p) {
   sb->dterms.upload(dg, c.stream);
   sb->n_dtasks = int(dt.size());
   if (c.opt.precision != DMRG_FP64) {
-    sb->L.data32.alloc(std::max<int64_t>(sb->L.n_elems, 1));
-    sb->R.data32.alloc(std::max<int64_t>(sb->R.n_elems, 1));
+    sb->L.data32.alloc(sb->L.n_elems + 4);
+    sb->R.data32.alloc(sb->R.n_elems + 4);
     to_f32(sb->L.data.p, sb->L.data32.p, sb->L.n_elems, c.stream);
     to_f32(sb->R.data.p, sb->R.data32.p, sb->R.n_elems, c.stream);
   }
@@ -572,32 +723,54 @@ static Super& super_at(Ctx& c, int p) {
   return *c.sb;
 }
 
+// two-stage H_eff lists (T = psi R^T, then psi' = sum s L T) used by the allocation-free
+// entry point; built by the allocating ABI calls only
+static void ensure_two_stage(Ctx& c, Super& sb) {
+  if (sb.two_stage_ready) return;
+  TaskList s1, s2;
+  int64_t toff = 0;
+  int last_out = -1;
+  for (const auto& it : sb.terms_host) {
+    const int dLi = sb.bdl[it.bin], dRi = sb.bdr[it.bin];
+    const int dLo = sb.bdl[it.bout], dRo = sb.bdr[it.bout];
+    if (it.bout != last_out) {
+      s2.begin_task(Operand{sb.boff[it.bout], B_Y, dRo}, dLo, dRo);
+      last_out = it.bout;
+    }
+    s1.begin_task(Operand{toff, B_T, dRo}, dLi, dRo);
+    s1.add_term(Operand{sb.boff[it.bin], B_X, dRi}, Operand{sb.R.blocks[it.rb].off, B_ROPS, dRi},
+                dRi, 2, 1.0);
+    s2.add_term(Operand{sb.L.blocks[it.lb].off, B_LOPS, dLi}, Operand{toff, B_T, dRo}, dLi, 0,
+                it.sign);
+    toff += int64_t(dLi) * dRo;
+  }
+  DMRG_REQUIRE(toff == sb.t_elems, DMRG_EINVAL, "internal: two-stage intermediate size");
+  int64_t be[NBASE] = {0};
+  be[B_X] = sb.size;
+  be[B_Y] = sb.size;
+  be[B_T] = sb.t_elems;
+  be[B_LOPS] = sb.L.n_elems;
+  be[B_ROPS] = sb.R.n_elems;
+  sb.st1.build(s1, be, c.stream);
+  sb.st2.build(s2, be, c.stream);
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sb.two_stage_ready = true;
+}
+
 static void heff(Ctx& c, Super& sb, const double* x, double* y) {
-  c.T.alloc(std::max<int64_t>(sb.t_elems, 1));
+  // every psi' element is written by exactly one fused tile (blocks without terms get
+  // zero-term tiles), so no clearing pass is needed
   if (c.opt.precision == DMRG_FP64) {
-    DMRG_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * sb.size, c.stream));
-    Bases<double> b{};
-    b.p[B_LOPS] = sb.L.data.p;
-    b.p[B_ROPS] = sb.R.data.p;
-    b.p[B_X] = const_cast<double*>(x);
-    b.p[B_Y] = y;
-    b.p[B_T] = c.T.p;
-    run_gemm_tasks<double>(sb.st1, b, 1, c.stream);
-    run_gemm_tasks<double>(sb.st2, b, 1, c.stream);
+    c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
+    heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, sb.L.data.p,
+                       sb.R.data.p, x, y, c.part64.p, c.stream);
   } else {
     c.f32a.alloc(std::max<int64_t>(sb.size, 1));
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
-    c.f32T.alloc(std::max<int64_t>(sb.t_elems, 1));
+    c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
     to_f32(x, c.f32a.p, sb.size, c.stream);
-    DMRG_CUDA(cudaMemsetAsync(c.f32b.p, 0, sizeof(float) * sb.size, c.stream));
-    Bases<float> b{};
-    b.p[B_LOPS] = sb.L.data32.p;
-    b.p[B_ROPS] = sb.R.data32.p;
-    b.p[B_X] = c.f32a.p;
-    b.p[B_Y] = c.f32b.p;
-    b.p[B_T] = c.f32T.p;
-    run_gemm_tasks<float>(sb.st1, b, 1, c.stream);
-    run_gemm_tasks<float>(sb.st2, b, 1, c.stream);
+    heff_fused<float>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred,
+                      sb.L.data32.p, sb.R.data32.p, c.f32a.p, c.f32b.p, c.part32.p, c.stream);
     to_f64(c.f32b.p, y, sb.size, c.stream);
   }
 }
@@ -705,6 +878,7 @@ struct DavResult {
 };
 
 static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
+  PhaseTimer tm(c.t_davidson);
   const int64_t n = sb.size;
   const int sub = std::max(4, std::min(64, c.opt.dav_max_sub));
   ensure_ws(c, n, sub);
@@ -811,6 +985,7 @@ struct TruncResult {
 };
 
 static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
+  PhaseTimer tm(c.t_truncate);
   DMRG_REQUIRE(c.sb && c.sb->p == p && c.psi_valid && c.psi_p == p, DMRG_EINVAL,
                "no eigenvector held for this position (call dmrg_davidson first)");
   DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
@@ -926,6 +1101,7 @@ static void uniform_guess(Ctx& c, Super& sb, double* g) {
 }
 
 static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
+  PhaseTimer tm(c.t_predict);
   cudaStream_t s = c.stream;
   if (!c.psi_valid || !c.prev) {
     uniform_guess(c, sb, g);
@@ -1159,7 +1335,7 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
 }
 
 bool heff_view(dmrg_ctx* c, int p, HeffView* v) {
-  if (!c || !c->sb || c->sb->p != p) return false;
+  if (!c || !c->sb || c->sb->p != p || !c->sb->two_stage_ready) return false;
   Super& sb = *c->sb;
   v->st1 = &sb.st1;
   v->st2 = &sb.st2;
@@ -1185,6 +1361,11 @@ using namespace dmrg;
 template <class F>
 static int guarded(dmrg_ctx* c, F&& f) {
   if (!c) return DMRG_EINVAL;
+  struct PoolScope {
+    Pool* prev;
+    explicit PoolScope(Pool* p) : prev(tl_pool) { tl_pool = p; }
+    ~PoolScope() { tl_pool = prev; }
+  } scope(&c->pool);
   try {
     f();
     return DMRG_OK;
@@ -1224,6 +1405,8 @@ extern "C" int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dm
     build_reach(*c);
     c->w_by_b.resize(c->N);
     c->w_by_a.resize(c->N);
+    c->ent_left.resize(c->N);
+    c->ent_right.resize(c->N);
     for (int s = 0; s < c->N; ++s) {
       const auto& W = c->mpo.W[s];
       std::vector<int> idx(W.size());
@@ -1265,6 +1448,7 @@ extern "C" int dmrg_psi_layout(dmrg_ctx* c, int32_t p, int64_t* n_blocks, int64_
                                int32_t* qn_left, int32_t* dl, int32_t* dr, int64_t* off) {
   return guarded(c, [&] {
     Super& sb = super_at(*c, p);
+    ensure_two_stage(*c, sb);
     if (n_blocks) *n_blocks = int64_t(sb.bL.size());
     if (size) *size = sb.size;
     for (size_t b = 0; b < sb.bL.size(); ++b) {
@@ -1285,6 +1469,7 @@ extern "C" int dmrg_heff_apply(dmrg_ctx* c, int32_t p, const double* x, double* 
   return guarded(c, [&] {
     DMRG_REQUIRE(x && y && x != y, DMRG_EINVAL, "bad vectors");
     Super& sb = super_at(*c, p);
+    ensure_two_stage(*c, sb);
     heff(*c, sb, x, y);
     DMRG_CUDA(cudaStreamSynchronize(c->stream));
   });
@@ -1413,6 +1598,12 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->heff_seconds = c->heff_seconds;
     out->heff_flops = c->heff_flops;
     out->heff_bytes = c->heff_bytes;
+    out->t_enlarge = c->t_enlarge;
+    out->t_super = c->t_super;
+    out->t_davidson = c->t_davidson;
+    out->t_truncate = c->t_truncate;
+    out->t_project = c->t_project;
+    out->t_predict = c->t_predict;
   });
 }
 

@@ -239,6 +239,71 @@ template void run_copy_tasks<float>(const CopyTask*, int64_t, const CopyTerm*,
                                     const Bases<float>&, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
+// enlargement: one warp assembles one block of an enlarged operator from the block
+// operators of the previous bond and the site operators of its W entries
+// ------------------------------------------------------------------------------------
+__constant__ int8_t c_op_entries[4][2][2] = {
+    {{0, 0}, {1, 1}}, {{1, 1}, {-1, -1}}, {{1, 0}, {-1, -1}}, {{0, 1}, {-1, -1}}};
+
+__global__ void __launch_bounds__(256) k_enlarge(const EnlBlock* __restrict__ blocks, int64_t n,
+                                                 const int32_t* __restrict__ eptr,
+                                                 const EntryDev* __restrict__ ents,
+                                                 const int32_t* __restrict__ by_in, int nsrc,
+                                                 const int64_t* __restrict__ boff,
+                                                 const int32_t* __restrict__ dim,
+                                                 const int32_t* __restrict__ npart,
+                                                 const int8_t* __restrict__ lpar,
+                                                 const LayDev* __restrict__ lay, int left,
+                                                 const double* __restrict__ src,
+                                                 double* __restrict__ out) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
+  const int lane = threadIdx.x & (kWarp - 1);
+  if (w >= n) return;
+  const EnlBlock b = blocks[w];
+  const LayDev lo = lay[b.Qo], li = lay[b.Qi];
+  double* dst = out + b.off;
+  const int Di = li.D;
+  for (int idx = lane; idx < lo.D * Di; idx += kWarp) dst[idx] = 0.0;
+  __syncwarp();
+  for (int x = eptr[b.k]; x < eptr[b.k + 1]; ++x) {
+    const EntryDev e = ents[x];
+    for (int y = 0; y < 2; ++y) {
+      const int so = c_op_entries[e.op][y][0], si = c_op_entries[e.op][y][1];
+      if (so < 0) continue;
+      const int qo = so ? lo.pblk1 : lo.pblk0, qi = si ? li.pblk1 : li.pblk0;
+      if (qo < 0 || qi < 0) continue;
+      const int sb = by_in[int64_t(e.src) * nsrc + qi];
+      if (sb < 0) continue;
+      double sc = e.coef;
+      if (left) {
+        if (e.op >= 2 && (npart[qi] & 1)) sc = -sc;
+      } else {
+        if (si && lpar[e.src]) sc = -sc;
+      }
+      const int rows = dim[qo], cols = dim[qi];
+      const int ro = so ? lo.poff1 : 0, ri = si ? li.poff1 : 0;
+      const double* S = src + boff[sb];
+      for (int idx = lane; idx < rows * cols; idx += kWarp) {
+        const int r = idx / cols, cc = idx - r * cols;
+        dst[(int64_t)(ro + r) * Di + ri + cc] += sc * S[idx];
+      }
+    }
+  }
+}
+
+void enlarge_blocks(const EnlBlock* blocks, int64_t n, const int32_t* eptr, const EntryDev* ents,
+                    const int32_t* src_by_in, int src_nsec, const int64_t* src_boff,
+                    const int32_t* src_dim, const int32_t* src_npart, const int8_t* src_lpar,
+                    const LayDev* lay, int left, const double* src, double* out, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t threads = n * kWarp;
+  k_enlarge<<<int((threads + 255) / 256), 256, 0, s>>>(blocks, n, eptr, ents, src_by_in, src_nsec,
+                                                       src_boff, src_dim, src_npart, src_lpar, lay,
+                                                       left, src, out);
+  DMRG_LAUNCHED();
+}
+
+// ------------------------------------------------------------------------------------
 // vector kernels
 // ------------------------------------------------------------------------------------
 constexpr int kDotBlocks = 264;   // fixed grid => fixed reduction order
