@@ -375,6 +375,9 @@ struct HeffRed {
   int64_t yoff, poff;
   int32_t ld, r0, c0, m, n, groups;
 };
+template <class TO>
+void pad_psi(const double* x, TO* xp, const int64_t* src_off, const int64_t* dst_off,
+             const int32_t* len, int nblocks, cudaStream_t s);
 template <class T>
 void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
                 const HeffRed* d_red, int64_t n_red, const T* L, const T* R, const T* X, T* Y,

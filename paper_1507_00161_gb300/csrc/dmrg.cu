@@ -126,6 +126,11 @@ struct Super {
   DevBuf<HeffTile> ftiles;
   DevBuf<HeffRed> fred;
   int64_t n_ftiles = 0, n_fred = 0, p_elems = 0;
+  // 16-byte aligned copy of psi used by the fused product
+  std::vector<int64_t> pad_off;
+  int64_t pad_size = 0;
+  DevBuf<int64_t> d_src_off, d_pad_off;
+  DevBuf<int32_t> d_pad_len;
   int64_t t_elems = 0;
   double flops = 0, bytes = 0;
   int64_t n_items = 0;
@@ -165,7 +170,8 @@ struct dmrg_ctx {
   // scratch
   dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
   dmrg::DevBuf<float> f32a, f32b, f32T, part32;
-  dmrg::DevBuf<double> part64;
+  dmrg::DevBuf<double> part64, xpad64;
+  dmrg::DevBuf<float> xpad32;
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
   std::vector<dmrg::SiteEntries> ent_left, ent_right;
@@ -532,6 +538,20 @@ static void build_super(Ctx& c, int p) {
     off += int64_t(sb->Ll.sec.d[i]) * sb->Rl.sec.d[j];
   }
   sb->size = off;
+  {
+    int64_t po = 0;
+    std::vector<int32_t> len(sb->bL.size());
+    for (size_t b = 0; b < sb->bL.size(); ++b) {
+      po = (po + 3) & ~int64_t(3);
+      sb->pad_off.push_back(po);
+      len[b] = sb->bdl[b] * sb->bdr[b];
+      po += len[b];
+    }
+    sb->pad_size = po + 4;
+    sb->d_src_off.upload(sb->boff, c.stream);
+    sb->d_pad_off.upload(sb->pad_off, c.stream);
+    sb->d_pad_len.upload(len, c.stream);
+  }
   // H_eff items: (label k, L block, R block)
   const auto& par = c.mpo.parity[p + 1];
   const int nlab = sb->L.nlab;
@@ -580,7 +600,7 @@ static void build_super(Ctx& c, int p) {
         HeffItem h;
         h.loff = sb->L.blocks[it.lb].off;
         h.roff = sb->R.blocks[it.rb].off;
-        h.xoff = sb->boff[it.bin];
+        h.xoff = sb->pad_off[it.bin];
         h.dLi = dLi;
         h.dRi = dRi;
         h.sign = float(it.sign);
@@ -667,7 +687,7 @@ static void build_super(Ctx& c, int p) {
         const HeffItem& h = fi[j];
         DMRG_REQUIRE(h.loff + int64_t(t.r0 + t.m) * h.dLi - 1 < sb->L.n_elems &&
                          h.roff + int64_t(t.c0 + t.n) * h.dRi - 1 < sb->R.n_elems &&
-                         h.xoff + int64_t(h.dLi) * h.dRi - 1 < sb->size,
+                         h.xoff + int64_t(h.dLi) * h.dRi - 1 < sb->pad_size - 4,
                      DMRG_EINVAL, "internal: fused item out of range");
       }
     }
@@ -760,17 +780,20 @@ static void ensure_two_stage(Ctx& c, Super& sb) {
 static void heff(Ctx& c, Super& sb, const double* x, double* y) {
   // every psi' element is written by exactly one fused tile (blocks without terms get
   // zero-term tiles), so no clearing pass is needed
+  const int nb = int(sb.bL.size());
   if (c.opt.precision == DMRG_FP64) {
     c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
+    c.xpad64.alloc(sb.pad_size);
+    pad_psi<double>(x, c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
     heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, sb.L.data.p,
-                       sb.R.data.p, x, y, c.part64.p, c.stream);
+                       sb.R.data.p, c.xpad64.p, y, c.part64.p, c.stream);
   } else {
-    c.f32a.alloc(std::max<int64_t>(sb.size, 1));
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
     c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
-    to_f32(x, c.f32a.p, sb.size, c.stream);
+    c.xpad32.alloc(sb.pad_size);
+    pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
     heff_fused<float>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred,
-                      sb.L.data32.p, sb.R.data32.p, c.f32a.p, c.f32b.p, c.part32.p, c.stream);
+                      sb.L.data32.p, sb.R.data32.p, c.xpad32.p, c.f32b.p, c.part32.p, c.stream);
     to_f64(c.f32b.p, y, sb.size, c.stream);
   }
 }

@@ -1,140 +1,222 @@
 // Fused superblock product  psi'(b') = sum_k s_k L_k[Q_L' <- Q_L] psi(b) R_k[Q_R' <- Q_R]^T
 // (the two-site H_eff of the superblock "Xi_l (x) Lambda (x) Lambda (x) Xi_r").
 //
-// One thread block per group of at most 64 terms of an output tile (at most 32 x 32 of a
-// psi' block), four warps splitting the group's terms; tiles with more terms write partial
-// tiles that a second kernel adds in group order.  Per term a warp stages the operator blocks it needs in shared memory
-// (16-byte vector loads when a block is contiguous: block offsets are 16-byte aligned),
-// forms X = psi_in R^T in shared memory (lanes over X elements), and accumulates s L X
-// into registers (lanes over output elements, so small blocks keep the lanes busy).
-// Inner dimensions are processed in chunks of 16.  The warps' partial tiles are added in a
-// fixed order: deterministic, no atomics.  Every
-// operator block is read once per product (outputs wider than one tile re-read the rows
-// they need), so the product is bound by HBM bandwidth.
+// Work unit (one thread block, four warps): a group of at most 64 terms of one output
+// tile (at most 32 x 32 of a psi' block).  Each warp takes every fourth term of the group.
+// Operator blocks and psi blocks start on 16-byte boundaries, so a warp streams the three
+// blocks of a term (L rows of the tile, R rows of the tile, psi_in) into a shared-memory
+// ring with 16-byte cp.async copies, up to four terms ahead of the one it computes
+// (completion in commit-group order; no spin-waits).  Compute from shared memory with a
+// fixed lane map: lane = (column c, row group g), rows g, g+G, ... with G = 32 / n:
+//     X[i][c] = sum_r psi[i][r] R[c][r]        (X in shared memory)
+//     acc[i][c] += s sum_k L[i][k] X[k][c]     (acc in registers)
+// Terms whose inner dimensions exceed 32 go through a chunked path that reads global
+// memory directly.  The warps' partial tiles are added in a fixed order, and groups of one
+// tile are added in group order by k_heff_reduce: the result is deterministic.
 #include <stdint.h>
 
 #include "common.h"
 
 namespace dmrg {
 
-constexpr int kC = 32;   // output tile edge
-constexpr int kK = 16;   // inner chunk
-constexpr int kW = 4;    // warps per block
-constexpr int kLS = kC * kK + 8;
-constexpr int kRS = kC * kK + 8;
-constexpr int kXS = kK * kC + 8;
-constexpr int kPerWarp = kLS + kRS + kXS;   // >= kC * kC: reused for the reduction
+constexpr int kW = 4;          // warps per block
+constexpr int kT = 32;         // output tile edge, small-term inner limit
+constexpr int kDepth = 4;      // terms in flight per warp
+constexpr int kRingBytes = 12288;
+constexpr int kXS = kT * (kT + 1);
 
-template <class T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using type = float4;
-  static constexpr int n = 4;
-};
-template <>
-struct Vec16<double> {
-  using type = double2;
-  static constexpr int n = 2;
-};
-
-// rows x cols of a row-major source (leading dimension ld) into dst (leading dimension
-// cols); 16-byte vectors when the region is contiguous and aligned (may write up to one
-// vector past rows*cols: the buffers are padded)
-template <class T>
-__device__ __forceinline__ void warp_stage(T* __restrict__ dst, const T* __restrict__ src, int rows,
-                                           int cols, int ld, int lane) {
-  using V = typename Vec16<T>::type;
-  constexpr int VN = Vec16<T>::n;
-  const int tot = rows * cols;
-  if (cols == ld && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-    const int nv = (tot + VN - 1) / VN;
-    const V* s = reinterpret_cast<const V*>(src);
-    V* d = reinterpret_cast<V*>(dst);
-    for (int v = lane; v < nv; v += 32) d[v] = __ldg(s + v);
-  } else {
-    for (int e = lane; e < tot; e += 32) {
-      const int r = e / cols, c = e - r * cols;
-      dst[e] = __ldg(src + (int64_t)r * ld + c);
-    }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_n(int n) {
+  switch (n) {
+    case 0: cp_wait<0>(); break;
+    case 1: cp_wait<1>(); break;
+    case 2: cp_wait<2>(); break;
+    default: cp_wait<3>(); break;
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 6 : 3) k_heff_fused(const HeffTile* __restrict__ tiles,
-                                                           const HeffItem* __restrict__ items,
-                                                           const T* __restrict__ L,
-                                                           const T* __restrict__ R,
-                                                           const T* __restrict__ X,
-                                                           T* __restrict__ Y,
-                                                           T* __restrict__ P) {
+__device__ __forceinline__ int round_vec(int e) {
+  constexpr int v = 16 / int(sizeof(T));
+  return (e + v - 1) / v * v;
+}
+
+// elements a small term occupies in the ring (three 16-byte aligned pieces)
+template <class T>
+__device__ __forceinline__ int term_elems(int m, int n, int dLi, int dRi) {
+  return round_vec<T>(m * dLi) + round_vec<T>(n * dRi) + round_vec<T>(dLi * dRi);
+}
+
+template <class T>
+__device__ __forceinline__ void stage(T* dst, const T* src, int elems, int lane) {
+  const int nv = (elems * int(sizeof(T)) + 15) / 16;
+  for (int v = lane; v < nv; v += 32)
+    cp_async16(reinterpret_cast<char*>(dst) + 16 * v, reinterpret_cast<const char*>(src) + 16 * v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 4 : 2)
+    k_heff_fused(const HeffTile* __restrict__ tiles, const HeffItem* __restrict__ items,
+                 const T* __restrict__ L, const T* __restrict__ R, const T* __restrict__ X,
+                 T* __restrict__ Y, T* __restrict__ P) {
+  constexpr int kRing = kRingBytes / int(sizeof(T));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* const base = reinterpret_cast<T*>(smem_raw);
-  const HeffTile t = tiles[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* const Ls = base + warp * kPerWarp;
-  T* const Rs = Ls + kLS;
-  T* const Xs = Rs + kRS;
-  const int m = t.m, n = t.n, mn = m * n;
-  T acc[kC];
+  T* const ring = base + warp * (kRing + kXS);
+  T* const Xs = ring + kRing;
+  __shared__ int slot_pos[kW][kDepth];
+  const HeffTile t = tiles[blockIdx.x];
+  const int m = t.m, n = t.n;
+  const int G = 32 / n;                // row groups
+  const int c = lane % n, g = lane / n;
+  const bool act = g < G;
+  const int rows_mine = act ? (m - g + G - 1) / G : 0;   // rows g, g+G, ... < m
+  T acc[kT];
 #pragma unroll
-  for (int q = 0; q < kC; ++q) acc[q] = T(0);
-  for (int j = t.i0 + warp; j < t.i1; j += kW) {
-    const HeffItem it = items[j];
-    const int dLi = it.dLi, dRi = it.dRi;
+  for (int q = 0; q < kT; ++q) acc[q] = T(0);
+
+  const int first = t.i0 + warp;
+  const int cnt = first < t.i1 ? (t.i1 - first + kW - 1) / kW : 0;
+  // ring state: terms in flight occupy [headpos, tail) or, once wrapped,
+  // [headpos, end of the used part) and [0, tail)
+  int issued = 0, done = 0, inflight = 0, tail = 0, headpos = 0;
+  bool wrapped = false;
+
+  while (done < cnt) {
+    // prefetch following terms into the ring (circular, in order)
+    while (inflight < kDepth && issued < cnt) {
+      const HeffItem it = items[first + issued * kW];
+      const int S = term_elems<T>(m, n, it.dLi, it.dRi);
+      if (it.dLi > kT || it.dRi > kT || S > kRing) break;
+      int pos;
+      if (inflight == 0) {
+        pos = 0;
+        wrapped = false;
+      } else if (!wrapped) {
+        if (tail + S <= kRing) {
+          pos = tail;
+        } else if (S <= headpos) {
+          pos = 0;
+          wrapped = true;
+        } else {
+          break;
+        }
+      } else {
+        if (tail + S <= headpos) pos = tail;
+        else break;
+      }
+      T* dst = ring + pos;
+      stage(dst, L + it.loff + (int64_t)t.r0 * it.dLi, m * it.dLi, lane);
+      dst += round_vec<T>(m * it.dLi);
+      stage(dst, R + it.roff + (int64_t)t.c0 * it.dRi, n * it.dRi, lane);
+      dst += round_vec<T>(n * it.dRi);
+      stage(dst, X + it.xoff, it.dLi * it.dRi, lane);
+      cp_commit();
+      if (lane == 0) slot_pos[warp][issued % kDepth] = pos;
+      if (inflight == 0) headpos = pos;
+      tail = pos + S;
+      ++issued;
+      ++inflight;
+    }
+    const HeffItem it = items[first + done * kW];
     const T sg = T(it.sign);
-    for (int k0 = 0; k0 < dLi; k0 += kK) {
-      const int kc = min(kK, dLi - k0);
-      // X (kc x n) = psi_in[k0.., :] R[c0.., :]^T, inner dimension in chunks
-      for (int e = lane; e < kc * n; e += 32) Xs[e] = T(0);
-      for (int r0 = 0; r0 < dRi; r0 += kK) {
-        const int rc = min(kK, dRi - r0);
-        warp_stage(Rs, R + it.roff + (int64_t)t.c0 * dRi + r0, n, rc, dRi, lane);
-        __syncwarp();
-        const T* __restrict__ P = X + it.xoff + (int64_t)k0 * dRi + r0;
-        for (int e = lane; e < kc * n; e += 32) {
-          const int i = e / n, c = e - i * n;
-          const T* pr = P + (int64_t)i * dRi;
-          const T* rr = Rs + c * rc;
-          T s = T(0);
-          for (int r = 0; r < rc; ++r) s = fma(__ldg(pr + r), rr[r], s);
-          Xs[e] += s;
+    const int dLi = it.dLi, dRi = it.dRi;
+    if (inflight == 0) {
+      // large term: chunked, straight from global memory
+      ++issued;
+      for (int k0 = 0; k0 < dLi; k0 += kT) {
+        const int kc = min(kT, dLi - k0);
+        if (act) {
+          const T* rr = R + it.roff + (int64_t)(t.c0 + c) * dRi;
+          for (int i = g; i < kc; i += G) {
+            const T* pr = X + it.xoff + (int64_t)(k0 + i) * dRi;
+            T s = T(0);
+            for (int r = 0; r < dRi; ++r) s = fma(pr[r], rr[r], s);
+            Xs[i * (kT + 1) + c] = s;
+          }
         }
         __syncwarp();
-      }
-      warp_stage(Ls, L + it.loff + (int64_t)t.r0 * dLi + k0, m, kc, dLi, lane);
-      __syncwarp();
+        if (act) {
+          for (int k = 0; k < kc; ++k) {
+            const T xv = sg * Xs[k * (kT + 1) + c];
+            const T* lc = L + it.loff + (int64_t)(t.r0 + g) * dLi + k0 + k;
 #pragma unroll
-      for (int q = 0; q < kC; ++q) {
-        const int e = lane + 32 * q;
-        if (e < mn) {
-          const int i = e / n, c = e - i * n;
-          const T* lr = Ls + i * kc;
-          const T* xc = Xs + c;
-          T s = T(0);
-          for (int k = 0; k < kc; ++k) s = fma(lr[k], xc[k * n], s);
-          acc[q] = fma(sg, s, acc[q]);
+            for (int q = 0; q < kT; ++q)
+              if (q < rows_mine) acc[q] = fma(lc[(int64_t)q * G * dLi], xv, acc[q]);
+          }
         }
+        __syncwarp();
       }
-      __syncwarp();
+      ++done;
+      continue;
+    }
+    // wait for the oldest term in flight (later groups may still be pending)
+    cp_wait_n(inflight - 1);
+    __syncwarp();
+    const T* Ls = ring + slot_pos[warp][done % kDepth];
+    const T* Rs = Ls + round_vec<T>(m * dLi);
+    const T* Ps = Rs + round_vec<T>(n * dRi);
+    if (act) {
+      const T* rr = Rs + c * dRi;
+      for (int i = g; i < dLi; i += G) {
+        const T* pr = Ps + i * dRi;
+        T s = T(0);
+        for (int r = 0; r < dRi; ++r) s = fma(pr[r], rr[r], s);
+        Xs[i * (kT + 1) + c] = s;
+      }
+    }
+    __syncwarp();
+    if (act) {
+      const T* lr = Ls + g * dLi;
+      for (int k = 0; k < dLi; ++k) {
+        const T xv = sg * Xs[k * (kT + 1) + c];
+#pragma unroll
+        for (int q = 0; q < kT; ++q)
+          if (q < rows_mine) acc[q] = fma(lr[q * G * dLi + k], xv, acc[q]);
+      }
+    }
+    __syncwarp();
+    ++done;
+    --inflight;
+    if (inflight > 0) {
+      const int np = slot_pos[warp][done % kDepth];
+      if (np < headpos) wrapped = false;   // the head crossed into the wrapped part
+      headpos = np;
+    } else {
+      tail = headpos = 0;
+      wrapped = false;
     }
   }
-  // fixed-order reduction of the warps' partial tiles
+  cp_wait<0>();
+  // fixed-order reduction of the warps' partial tiles (reuses the rings)
   __syncthreads();
-  T* const red = base + warp * kPerWarp;
+  T* const red = base + warp * (kRing + kXS);
+  if (act) {
 #pragma unroll
-  for (int q = 0; q < kC; ++q) {
-    const int e = lane + 32 * q;
-    if (e < mn) red[e] = acc[q];
+    for (int q = 0; q < kT; ++q)
+      if (q < rows_mine) red[(g + q * G) * n + c] = acc[q];
   }
   __syncthreads();
+  const int mn = m * n;
   for (int e = threadIdx.x; e < mn; e += kW * 32) {
-    const int i = e / n, c = e - i * n;
     T s = base[e];
 #pragma unroll
-    for (int w = 1; w < kW; ++w) s += base[w * kPerWarp + e];
-    if (t.poff < 0) Y[t.yoff + (int64_t)(t.r0 + i) * t.ld + t.c0 + c] = s;
-    else P[t.poff + e] = s;
+    for (int w = 1; w < kW; ++w) s += base[w * (kRing + kXS) + e];
+    if (t.poff < 0) {
+      const int i = e / n, cc = e - i * n;
+      Y[t.yoff + (int64_t)(t.r0 + i) * t.ld + t.c0 + cc] = s;
+    } else {
+      P[t.poff + e] = s;
+    }
   }
 }
 
@@ -152,12 +234,23 @@ __global__ void k_heff_reduce(const HeffRed* __restrict__ red, const T* __restri
   }
 }
 
+// psi blocks into a 16-byte aligned copy (optionally converted): one block per thread block
+template <class TI, class TO>
+__global__ void k_pad_psi(const TI* __restrict__ x, TO* __restrict__ xp,
+                          const int64_t* __restrict__ src_off, const int64_t* __restrict__ dst_off,
+                          const int32_t* __restrict__ len) {
+  const int b = blockIdx.x;
+  const TI* s = x + src_off[b];
+  TO* d = xp + dst_off[b];
+  for (int i = threadIdx.x; i < len[b]; i += blockDim.x) d[i] = TO(s[i]);
+}
+
 template <class T>
 void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
                 const HeffRed* d_red, int64_t n_red, const T* L, const T* R, const T* X, T* Y,
                 T* partial, cudaStream_t s) {
   if (n_tiles <= 0) return;
-  const size_t smem = sizeof(T) * kW * kPerWarp;
+  const size_t smem = sizeof(T) * kW * (kRingBytes / sizeof(T) + kXS);
   static bool attr_set = false;   // per process: the attribute belongs to the kernel
   if (!attr_set) {
     DMRG_CUDA(cudaFuncSetAttribute(k_heff_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -177,5 +270,17 @@ template void heff_fused<double>(const HeffTile*, int64_t, const HeffItem*, cons
 template void heff_fused<float>(const HeffTile*, int64_t, const HeffItem*, const HeffRed*,
                                 int64_t, const float*, const float*, const float*, float*,
                                 float*, cudaStream_t);
+
+template <class TO>
+void pad_psi(const double* x, TO* xp, const int64_t* src_off, const int64_t* dst_off,
+             const int32_t* len, int nblocks, cudaStream_t s) {
+  if (nblocks <= 0) return;
+  k_pad_psi<double, TO><<<nblocks, 128, 0, s>>>(x, xp, src_off, dst_off, len);
+  DMRG_LAUNCHED();
+}
+template void pad_psi<double>(const double*, double*, const int64_t*, const int64_t*,
+                              const int32_t*, int, cudaStream_t);
+template void pad_psi<float>(const double*, float*, const int64_t*, const int64_t*,
+                             const int32_t*, int, cudaStream_t);
 
 }  // namespace dmrg

@@ -122,3 +122,41 @@ def test_full_m_reproduces_exact_diagonalization(P):
     steps, e = d.sweep(400)
     assert abs(e - e0) < 1e-9
     assert max(s["trunc_err"] for s in steps) < 1e-12
+
+
+def test_fused_product_matches_two_stage(P):
+    """Superblocks with sectors wider than 32 (chunked path, ring wrap-around), found near
+    both ends of the chain after a sweep: the fused H_eff kernel against the independent
+    two-stage task-list product (the allocation-free entry point) in FP64, and the FP32
+    fused product against both."""
+    prob = make_problem("pf", 4, 4, 0, seed=2)
+    d = P.DMRG(prob)
+    d.build_blocks(initial_mps(prob, 2048, 2002))
+    d.sweep(2048)
+    N = prob.n_sites
+    rng = np.random.default_rng(19)
+    max_dl = max_dr = 0
+    checked = 0
+    for p in (2, 3, 5, N - 6, N - 4, N - 3):
+        lay = d.psi_layout(p)
+        x = torch.tensor(rng.standard_normal(lay["size"]), dtype=torch.float64, device="cuda")
+        y1 = torch.empty_like(x)
+        y2 = torch.empty_like(x)
+        d.heff_apply(p, x, y1)
+        try:
+            d.heff_apply_noalloc(p, x, y2)
+        except P.DmrgError:
+            continue          # intermediate larger than the fixed scratch
+        err = (torch.linalg.norm(y1 - y2) / torch.linalg.norm(y2)).item()
+        assert err <= 1e-12, (p, err)
+        d.set_options(precision=P.MIXED_FP32)
+        y3 = torch.empty_like(x)
+        d.heff_apply(p, x, y3)
+        d.set_options(precision=P.FP64)
+        err32 = (torch.linalg.norm(y3 - y2) / torch.linalg.norm(y2)).item()
+        assert err32 <= 1e-5, (p, err32)
+        max_dl = max(max_dl, int(lay["dl"].max()))
+        max_dr = max(max_dr, int(lay["dr"].max()))
+        checked += 1
+    assert checked >= 4
+    assert max_dl > 32 and max_dr > 32, (max_dl, max_dr)
