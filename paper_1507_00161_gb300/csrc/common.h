@@ -375,6 +375,12 @@ struct HeffRed {
   int64_t yoff, poff;
   int32_t ld, r0, c0, m, n, groups;
 };
+template <class T>
+void heff_reduce(const HeffRed* d_red, int64_t n_red, const T* partial, T* Y, cudaStream_t s);
+// mixed path: the same product with 3xTF32 warp MMAs (heff_tc.cu)
+void heff_tc(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
+             const HeffRed* d_red, int64_t n_red, const float* L, const float* R, const float* X,
+             float* Y, float* partial, cudaStream_t s);
 template <class TO>
 void pad_psi(const double* x, TO* xp, const int64_t* src_off, const int64_t* dst_off,
              const int32_t* len, int nblocks, cudaStream_t s);

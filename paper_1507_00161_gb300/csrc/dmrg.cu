@@ -792,8 +792,8 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y) {
     c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad32.alloc(sb.pad_size);
     pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
-    heff_fused<float>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred,
-                      sb.L.data32.p, sb.R.data32.p, c.xpad32.p, c.f32b.p, c.part32.p, c.stream);
+    heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, sb.L.data32.p,
+            sb.R.data32.p, c.xpad32.p, c.f32b.p, c.part32.p, c.stream);
     to_f64(c.f32b.p, y, sb.size, c.stream);
   }
 }

@@ -246,6 +246,15 @@ __global__ void k_pad_psi(const TI* __restrict__ x, TO* __restrict__ xp,
 }
 
 template <class T>
+void heff_reduce(const HeffRed* d_red, int64_t n_red, const T* partial, T* Y, cudaStream_t s) {
+  if (n_red <= 0) return;
+  k_heff_reduce<T><<<int(n_red), 128, 0, s>>>(d_red, partial, Y);
+  DMRG_LAUNCHED();
+}
+template void heff_reduce<float>(const HeffRed*, int64_t, const float*, float*, cudaStream_t);
+template void heff_reduce<double>(const HeffRed*, int64_t, const double*, double*, cudaStream_t);
+
+template <class T>
 void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
                 const HeffRed* d_red, int64_t n_red, const T* L, const T* R, const T* X, T* Y,
                 T* partial, cudaStream_t s) {

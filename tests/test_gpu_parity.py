@@ -53,6 +53,11 @@ def test_heff_first_position(P, space, Np, Nn, seed, M0):
         d.heff_apply(1, xd, yd)
         y = yd.cpu().numpy()
         assert np.linalg.norm(y - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
+    # mixed path (FP32 storage, split-TF32 tensor-core products): FP32-level accuracy
+    d.set_options(precision=P.MIXED_FP32)
+    d.heff_apply(1, xd, yd)
+    y = yd.cpu().numpy()
+    assert np.linalg.norm(y - y_ref) <= 2e-6 * np.linalg.norm(y_ref)
 
 
 @pytest.mark.parametrize("space,Np,Nn,seed,M0", CASES[:2])
