@@ -42,6 +42,9 @@ extern "C" {
 #define DMRG_FP64 0         /* every contraction in FP64                               */
 #define DMRG_MIXED_FP32 1   /* operator contractions in FP32, Davidson/eig/energy FP64 */
 
+#define DMRG_PRECOND_DIAG 0 /* Davidson correction r_i / (theta - D_i)                  */
+#define DMRG_PRECOND_MLP 1  /* learned correction (falls back to DIAG until trained)    */
+
 typedef struct dmrg_ctx dmrg_ctx;
 
 /* The shell-model Hamiltonian of Eq. (1) on m-scheme orbitals alpha = (n,l,j,m,tau_z):
@@ -62,7 +65,7 @@ typedef struct {
 
 typedef struct {
   int32_t precision;        /* DMRG_FP64 or DMRG_MIXED_FP32                            */
-  int32_t reserved0;
+  int32_t reserved0;        /* preconditioner: DMRG_PRECOND_DIAG or DMRG_PRECOND_MLP   */
   double dav_tol;           /* Davidson residual-norm tolerance (MeV), e.g. 1e-8       */
   int32_t dav_max_iter;     /* maximum H_eff products per step, e.g. 100               */
   int32_t dav_max_sub;      /* subspace size before thick restart, 4..64, e.g. 24      */
@@ -205,6 +208,31 @@ int dmrg_heff_apply_noalloc(dmrg_ctx* ctx, int32_t p, const double* psi_in_dev,
  * products, so the stopping test uses max(dav_tol, 1e-6 |theta|); the reported energy
  * is the FP64 Rayleigh quotient of the converged vector. */
 int dmrg_set_options(dmrg_ctx* ctx, const dmrg_options* opt);
+
+/* Learned Davidson preconditioner (not in the paper).  A network maps four features of
+ * each wave-function element (asinh(theta - D_i), r_i and x_i normalised, the diagonal
+ * correction normalised) through three ReLU layers of width 256 to the element of the
+ * correction; it is trained on pairs that diagonal Davidson steps of this context
+ * produce (target: the converged eigenvector's component orthogonal to the iterate) with
+ * the library's own forward, backward and Adam kernels.  The preconditioner changes only
+ * how the Davidson subspace grows, never the converged eigenpair.
+ *   dmrg_mlp_reset: He-normal weights from a seed (SplitMix64), zero biases.
+ *   dmrg_mlp_harvest: when enable != 0, every later Davidson run stores training pairs
+ *     from its first eight iterates, per_iter elements each (fixed stride).
+ *   dmrg_mlp_train: epochs of Adam over the harvested pairs, minibatch size batch;
+ *     loss = mean squared error of the last epoch.  DMRG_EINVAL without samples.
+ *   dmrg_mlp_params: dir 0 copies the parameters to host, dir 1 sets them (n must be
+ *     dmrg_mlp_n_params()).  Packing: W1 (256x4), b1, W2 (256x256), b2, W3, b3, w4, b4.
+ *   dmrg_mlp_loss_grad: loss and parameter gradient on given samples (B rows of 4
+ *     features, B targets) in DMRG_FP64 or DMRG_MIXED_FP32 arithmetic (checks). */
+int dmrg_mlp_reset(dmrg_ctx* ctx, uint64_t seed);
+int dmrg_mlp_harvest(dmrg_ctx* ctx, int32_t enable, int32_t per_iter);
+int dmrg_mlp_train(dmrg_ctx* ctx, int32_t epochs, int32_t batch, double lr, uint64_t seed,
+                   double* loss, int64_t* n_samples);
+int dmrg_mlp_params(dmrg_ctx* ctx, int32_t dir, double* host, int64_t n);
+int dmrg_mlp_loss_grad(dmrg_ctx* ctx, int32_t precision, const double* params, const double* X,
+                       const double* T, int64_t B, double* loss, double* grad);
+int64_t dmrg_mlp_n_params(void);
 
 /* Read the cumulative counters. */
 int dmrg_get_counters(dmrg_ctx* ctx, dmrg_counters* out);

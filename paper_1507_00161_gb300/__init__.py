@@ -26,7 +26,10 @@ EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
             "dmrg_set_options", "dmrg_get_counters", "dmrg_heff_cost",
-            "dmrg_heff_apply_noalloc"]
+            "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
+            "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params"]
+PRECOND_DIAG = 0
+PRECOND_MLP = 1
 
 
 class DmrgError(RuntimeError):
@@ -110,6 +113,11 @@ def load_library(path: str = LIB_PATH):
         "dmrg_block_sectors": [P, i32, i32, P, P, P],
         "dmrg_heff_cost": [P, i32, P, P, P],
         "dmrg_set_options": [P, ctypes.POINTER(Options)],
+        "dmrg_mlp_reset": [P, ctypes.c_uint64],
+        "dmrg_mlp_harvest": [P, i32, i32],
+        "dmrg_mlp_train": [P, i32, i32, dbl, ctypes.c_uint64, P, P],
+        "dmrg_mlp_params": [P, i32, P, i64],
+        "dmrg_mlp_loss_grad": [P, i32, P, P, P, i64, P, P],
         "dmrg_get_counters": [P, ctypes.POINTER(Counters)],
     }
     for name, args in sig.items():
@@ -118,6 +126,8 @@ def load_library(path: str = LIB_PATH):
         f.restype = ctypes.c_int
     lib.dmrg_last_error.argtypes = [P]
     lib.dmrg_last_error.restype = ctypes.c_char_p
+    lib.dmrg_mlp_n_params.argtypes = []
+    lib.dmrg_mlp_n_params.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -139,7 +149,7 @@ class DMRG:
     """One problem (Eq. 1 on m-scheme sites, a target sector) on the GPU."""
 
     def __init__(self, problem, precision=FP64, dav_tol=1e-8, dav_max_iter=100, dav_max_sub=24,
-                 stream=None):
+                 stream=None, precond=PRECOND_DIAG):
         self.lib = load_library()
         self._keep = dict(
             species=np.ascontiguousarray(problem.species, dtype=np.int8),
@@ -156,7 +166,7 @@ class DMRG:
                      k["v_val"].ctypes.data if k["v_val"].size else None,
                      k["order"].ctypes.data, int(problem.Np), int(problem.Nn),
                      int(problem.two_Mz))
-        opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream)
+        opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream, precond)
         h = ctypes.c_void_p()
         rc = self.lib.dmrg_create(ctypes.byref(pr), ctypes.byref(opt), ctypes.byref(h))
         self.h = h.value
@@ -166,16 +176,16 @@ class DMRG:
             raise DmrgError(rc, msg)
 
     @staticmethod
-    def _options(precision, dav_tol, dav_max_iter, dav_max_sub, stream):
+    def _options(precision, dav_tol, dav_max_iter, dav_max_sub, stream, precond=PRECOND_DIAG):
         stream_ptr = None
         if stream is not None:
             stream_ptr = stream if isinstance(stream, int) else stream.cuda_stream
-        return Options(int(precision), 0, float(dav_tol), int(dav_max_iter), int(dav_max_sub),
-                       stream_ptr)
+        return Options(int(precision), int(precond), float(dav_tol), int(dav_max_iter),
+                       int(dav_max_sub), stream_ptr)
 
     def set_options(self, precision=FP64, dav_tol=1e-8, dav_max_iter=100, dav_max_sub=24,
-                    stream=None):
-        opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream)
+                    stream=None, precond=PRECOND_DIAG):
+        opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream, precond)
         self._check(self.lib.dmrg_set_options(self.h, ctypes.byref(opt)))
 
     def counters(self):
@@ -263,6 +273,41 @@ class DMRG:
         d = np.zeros(n.value, dtype=np.int32)
         self._check(self.lib.dmrg_block_sectors(self.h, side, b, None, _np_ptr(qn), _np_ptr(d)))
         return qn, d
+
+    # ---- learned preconditioner ----
+    def mlp_reset(self, seed=1):
+        self._check(self.lib.dmrg_mlp_reset(self.h, seed))
+
+    def mlp_harvest(self, enable=True, per_iter=2048):
+        self._check(self.lib.dmrg_mlp_harvest(self.h, 1 if enable else 0, per_iter))
+
+    def mlp_train(self, epochs=20, batch=4096, lr=1e-3, seed=1):
+        loss = ctypes.c_double()
+        ns = ctypes.c_int64()
+        self._check(self.lib.dmrg_mlp_train(self.h, epochs, batch, lr, seed, ctypes.byref(loss),
+                                            ctypes.byref(ns)))
+        return loss.value, ns.value
+
+    def mlp_params(self):
+        n = int(self.lib.dmrg_mlp_n_params())
+        out = np.zeros(n)
+        self._check(self.lib.dmrg_mlp_params(self.h, 0, _np_ptr(out), n))
+        return out
+
+    def mlp_set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(self.lib.dmrg_mlp_params(self.h, 1, _np_ptr(theta), theta.shape[0]))
+
+    def mlp_loss_grad(self, theta, X, T, precision=FP64):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        g = np.zeros_like(theta)
+        loss = ctypes.c_double()
+        self._check(self.lib.dmrg_mlp_loss_grad(self.h, precision, _np_ptr(theta), _np_ptr(X),
+                                                _np_ptr(T), X.shape[0], ctypes.byref(loss),
+                                                _np_ptr(g)))
+        return loss.value, g
 
     def heff_cost(self, p):
         f = ctypes.c_double()

@@ -407,6 +407,49 @@ void enlarge_blocks(const EnlBlock* blocks, int64_t n, const int32_t* eptr, cons
                     const int32_t* src_dim, const int32_t* src_npart, const int8_t* src_lpar,
                     const LayDev* lay, int left, const double* src, double* out, cudaStream_t s);
 
+// learned preconditioner (mlp.cu)
+template <class T>
+struct MlpActs {
+  DevBuf<T> Z1, H1, Z2, H2, Z3, H3, Y, dY, dH, dZ;
+  DevBuf<double> part;
+  int64_t cap = 0;
+  void ensure(int64_t B) {
+    if (B <= cap) return;
+    const int64_t nh = B * 256;
+    Z1.alloc(nh);
+    H1.alloc(nh);
+    Z2.alloc(nh);
+    H2.alloc(nh);
+    Z3.alloc(nh);
+    H3.alloc(nh);
+    dH.alloc(nh);
+    dZ.alloc(nh);
+    Y.alloc(B);
+    dY.alloc(B);
+    cap = B;
+  }
+};
+int64_t mlp_n_params();
+template <class T>
+void mlp_forward(const T* P, const T* X, int64_t B, MlpActs<T>& a, cudaStream_t s);
+template <class T>
+double mlp_backward(const T* P, const T* X, const T* Tg, int64_t B, MlpActs<T>& a, T* G,
+                    cudaStream_t s);
+template <class T>
+void mlp_adam(T* P, const T* G, T* m, T* v, int64_t n, double lr, int step, cudaStream_t s);
+template <class T>
+void mlp_gather(const T* S, const int32_t* idx, int64_t B, T* X, T* Tg, cudaStream_t s);
+template <class T>
+void mlp_features(const double* r, const double* x, const double* diag, const double* sc,
+                  int64_t n, T* X, cudaStream_t s);
+template <class T>
+void mlp_output_to_double(const T* y, double* out, int64_t n, cudaStream_t s);
+void mlp_harvest(const double* r, const double* x, const double* psi, const double* diag,
+                 const double* sc, int64_t n, int64_t start, int64_t stride, int64_t count,
+                 float* out, cudaStream_t s);
+void mlp_err_vec(const double* x, const double* psi, const double* sc, int64_t n, double* e,
+                 cudaStream_t s);
+
 // read-only view of the H_eff task lists of the superblock currently set up at position p
 // (nothing is built or allocated; false if the superblock at p is not set up)
 struct HeffView {

@@ -175,6 +175,15 @@ struct dmrg_ctx {
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
   std::vector<dmrg::SiteEntries> ent_left, ent_right;
+  // learned preconditioner: parameters, Adam moments, harvested samples, Davidson history
+  dmrg::DevBuf<float> mlp_p, mlp_g, mlp_m, mlp_v, mlp_samples, mlp_X, mlp_T, mlp_feat;
+  dmrg::MlpActs<float> mlp_acts;
+  dmrg::DevBuf<int32_t> mlp_idx;
+  bool mlp_ready = false, mlp_trained = false;
+  int mlp_step = 0;
+  int64_t mlp_nsamp = 0, mlp_cap = 262144, mlp_head = 0, mlp_calls = 0;
+  int mlp_harvest = 0, mlp_per_iter = 2048;
+  dmrg::DevBuf<double> hist_x, hist_r, hist_theta, hist_tmp, mlp_sc;
   // H_eff timing: event pairs recorded around every product, resolved after a sync
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
@@ -893,6 +902,37 @@ static void ensure_ws(Ctx& c, int64_t n, int sub) {
   c.ws_sub = sub;
 }
 
+// training pairs from the saved iterates of one Davidson run (psi = converged vector)
+static void harvest(Ctx& c, Super& sb, int nhist, const double* psi) {
+  cudaStream_t s = c.stream;
+  const int64_t n = sb.size, ld = c.ws_n;
+  double* part = c.partials.p;
+  c.mlp_samples.alloc(c.mlp_cap * 5);
+  const int64_t count = std::min<int64_t>(c.mlp_per_iter, n);
+  if (count <= 0) return;
+  const int64_t stride = std::max<int64_t>(1, n / count);
+  for (int h = 0; h < nhist; ++h) {
+    const double* xh = c.hist_x.p + h * ld;
+    const double* rh = c.hist_r.p + h * ld;
+    double* sc = c.mlp_sc.p + 16;   // {theta, |r|^2, |d|^2, x.psi, |e|^2}
+    DMRG_CUDA(cudaMemcpyAsync(sc, c.hist_theta.p + h, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    dot(rh, rh, n, sc + 1, part, s);
+    davidson_correction(rh, sb.diag.p, sc, n, c.hist_tmp.p, s);
+    dot(c.hist_tmp.p, c.hist_tmp.p, n, sc + 2, part, s);
+    dot(xh, psi, n, sc + 3, part, s);
+    mlp_err_vec(xh, psi, sc, n, c.hist_tmp.p, s);
+    dot(c.hist_tmp.p, c.hist_tmp.p, n, sc + 4, part, s);
+    if (c.mlp_head + count > c.mlp_cap) c.mlp_head = 0;
+    const int64_t start = (int64_t(h) * 131 + c.mlp_calls * 7) % stride;
+    const int64_t cnt = std::min<int64_t>(count, (n - 1 - start) / stride + 1);
+    mlp_harvest(rh, xh, psi, sb.diag.p, sc, n, start, stride, cnt,
+                c.mlp_samples.p + c.mlp_head * 5, s);
+    c.mlp_head += cnt;
+    c.mlp_nsamp = std::min<int64_t>(c.mlp_cap, c.mlp_nsamp + cnt);
+  }
+  ++c.mlp_calls;
+}
+
 struct DavResult {
   double theta = 0, resid = 0;
   int nprod = 0;
@@ -925,6 +965,16 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
   auto d2d = [&](double* dst, const double* src) {
     DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   };
+  const int kHist = 8;
+  int nhist = 0;
+  const bool use_mlp = c.opt.reserved0 == DMRG_PRECOND_MLP && c.mlp_trained;
+  if (c.mlp_harvest) {
+    c.hist_x.alloc(kHist * ld);
+    c.hist_r.alloc(kHist * ld);
+    c.hist_theta.alloc(kHist);
+    c.hist_tmp.alloc(ld);
+  }
+  c.mlp_sc.alloc(64);
   // v_0 = x0 / |x0|
   d2d(vec(0), guess);
   dot(vec(0), vec(0), n, sc, part, s);
@@ -948,6 +998,13 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
     res.theta = theta;
     res.resid = rn;
     res.nprod = nprod;
+    if (c.mlp_harvest && nhist < kHist) {   // iterate, residual and Ritz value for training
+      d2d(c.hist_x.p + nhist * ld, c.x.p);
+      d2d(c.hist_r.p + nhist * ld, c.r.p);
+      DMRG_CUDA(cudaMemcpyAsync(c.hist_theta.p + nhist, w, sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+      ++nhist;
+    }
     // FP32 products cannot resolve residuals below ~1e-7 of |H|: relative floor
     const double tol_eff =
         c.opt.precision == DMRG_FP64 ? tol : std::max(tol, 1e-6 * std::max(1.0, std::fabs(theta)));
@@ -955,8 +1012,18 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
       res.converged = rn <= tol_eff;
       break;
     }
-    // correction t = r / (theta - D), clamped
+    // correction: t = r / (theta - D), clamped (diagonal), or the learned map
     davidson_correction(c.r.p, sb.diag.p, w, n, c.t.p, s);
+    if (use_mlp) {
+      double* fs = c.mlp_sc.p + 8;
+      DMRG_CUDA(cudaMemcpyAsync(fs, w, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      dot(c.r.p, c.r.p, n, fs + 1, part, s);
+      dot(c.t.p, c.t.p, n, fs + 2, part, s);
+      c.mlp_feat.alloc(n * 4);
+      mlp_features<float>(c.r.p, c.x.p, sb.diag.p, fs, n, c.mlp_feat.p, s);
+      mlp_forward<float>(c.mlp_p.p, c.mlp_feat.p, n, c.mlp_acts, s);
+      mlp_output_to_double<float>(c.mlp_acts.Y.p, c.t.p, n, s);
+    }
     if (k >= sub) {   // thick restart from the two lowest Ritz vectors
       lincomb(Vp, Y + 64, k, n, c.x1.p, 0.0, 1.0, s);
       lincomb(AVp, Y + 64, k, n, c.Ax1.p, 0.0, 1.0, s);
@@ -994,6 +1061,7 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
     res.theta = h[0];
   }
   d2d(out, c.x.p);
+  if (c.mlp_harvest && nhist > 0) harvest(c, sb, nhist, c.x.p);
   res.heff_seconds = resolve_heff_timing(c);
   return res;
 }
@@ -1629,6 +1697,145 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->t_predict = c->t_predict;
   });
 }
+
+static uint64_t splitmix(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static void mlp_init(Ctx& c, uint64_t seed) {
+  const int64_t np = mlp_n_params();
+  std::vector<float> h(np, 0.0f);
+  // He-normal weights (Box-Muller on SplitMix64), zero biases
+  const int64_t sizes[4][3] = {{0, 256, 4}, {256 * 4 + 256, 256, 256},
+                               {256 * 4 + 256 + 256 * 256 + 256, 256, 256},
+                               {256 * 4 + 256 + 2 * (256 * 256 + 256), 1, 256}};
+  uint64_t st = seed;
+  for (auto& L : sizes) {
+    const double sd = std::sqrt(2.0 / double(L[2]));
+    for (int64_t i = 0; i < L[1] * L[2]; ++i) {
+      const double u1 = (splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+      const double u2 = (splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+      h[L[0] + i] = float(sd * std::sqrt(-2.0 * std::log(1.0 - u1)) * std::cos(6.283185307179586 * u2));
+    }
+  }
+  c.mlp_p.upload(h, c.stream);
+  c.mlp_g.alloc(np);
+  c.mlp_m.alloc(np);
+  c.mlp_v.alloc(np);
+  DMRG_CUDA(cudaMemsetAsync(c.mlp_m.p, 0, sizeof(float) * np, c.stream));
+  DMRG_CUDA(cudaMemsetAsync(c.mlp_v.p, 0, sizeof(float) * np, c.stream));
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  c.mlp_ready = true;
+  c.mlp_trained = false;
+  c.mlp_step = 0;
+}
+
+extern "C" int dmrg_mlp_reset(dmrg_ctx* c, uint64_t seed) {
+  return guarded(c, [&] { mlp_init(*c, seed); });
+}
+
+extern "C" int dmrg_mlp_harvest(dmrg_ctx* c, int32_t enable, int32_t per_iter) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(per_iter >= 1, DMRG_EINVAL, "per_iter must be positive");
+    c->mlp_harvest = enable ? 1 : 0;
+    c->mlp_per_iter = per_iter;
+  });
+}
+
+extern "C" int dmrg_mlp_train(dmrg_ctx* c, int32_t epochs, int32_t batch, double lr, uint64_t seed,
+                              double* loss_out, int64_t* n_samples) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(epochs >= 0 && batch >= 1 && lr > 0, DMRG_EINVAL, "bad training parameters");
+    DMRG_REQUIRE(c->mlp_nsamp > 0, DMRG_EINVAL, "no harvested samples");
+    if (!c->mlp_ready) mlp_init(*c, seed);
+    const int64_t ns = c->mlp_nsamp, np = mlp_n_params();
+    const int64_t B = std::min<int64_t>(batch, ns);
+    c->mlp_X.alloc(B * 4);
+    c->mlp_T.alloc(B);
+    c->mlp_idx.alloc(ns);
+    std::vector<int32_t> perm(ns);
+    uint64_t st = seed ^ 0x5DEECE66Dull;
+    double last = 0.0;
+    for (int e = 0; e < epochs; ++e) {
+      for (int64_t i = 0; i < ns; ++i) perm[i] = int32_t(i);
+      for (int64_t i = ns - 1; i > 0; --i) std::swap(perm[i], perm[splitmix(st) % uint64_t(i + 1)]);
+      c->mlp_idx.upload(perm, c->stream);
+      double tot = 0.0;
+      int nbat = 0;
+      for (int64_t b0 = 0; b0 + B <= ns; b0 += B) {
+        mlp_gather<float>(c->mlp_samples.p, c->mlp_idx.p + b0, B, c->mlp_X.p, c->mlp_T.p, c->stream);
+        mlp_forward<float>(c->mlp_p.p, c->mlp_X.p, B, c->mlp_acts, c->stream);
+        tot += mlp_backward<float>(c->mlp_p.p, c->mlp_X.p, c->mlp_T.p, B, c->mlp_acts, c->mlp_g.p,
+                                   c->stream);
+        ++nbat;
+        mlp_adam<float>(c->mlp_p.p, c->mlp_g.p, c->mlp_m.p, c->mlp_v.p, np, lr, ++c->mlp_step,
+                        c->stream);
+      }
+      last = nbat ? tot / nbat : 0.0;
+    }
+    DMRG_CUDA(cudaStreamSynchronize(c->stream));
+    c->mlp_trained = true;
+    if (loss_out) *loss_out = last;
+    if (n_samples) *n_samples = ns;
+  });
+}
+
+extern "C" int dmrg_mlp_params(dmrg_ctx* c, int32_t dir, double* host, int64_t n) {
+  return guarded(c, [&] {
+    const int64_t np = mlp_n_params();
+    DMRG_REQUIRE(host && n == np, DMRG_EINVAL, "parameter buffer must hold dmrg_mlp_n_params()");
+    std::vector<float> f(np);
+    if (dir == 0) {
+      DMRG_REQUIRE(c->mlp_ready, DMRG_EINVAL, "network not initialised");
+      DMRG_CUDA(cudaMemcpyAsync(f.data(), c->mlp_p.p, sizeof(float) * np, cudaMemcpyDeviceToHost,
+                                c->stream));
+      DMRG_CUDA(cudaStreamSynchronize(c->stream));
+      for (int64_t i = 0; i < np; ++i) host[i] = f[i];
+    } else {
+      if (!c->mlp_ready) mlp_init(*c, 1);
+      for (int64_t i = 0; i < np; ++i) f[i] = float(host[i]);
+      c->mlp_p.upload(f, c->stream);
+      DMRG_CUDA(cudaStreamSynchronize(c->stream));
+      c->mlp_trained = true;
+    }
+  });
+}
+
+template <class T>
+static double loss_grad_t(Ctx& c, const double* P, const double* X, const double* Tg, int64_t B,
+                          double* grad) {
+  const int64_t np = mlp_n_params();
+  std::vector<T> hp(P, P + np), hx(X, X + B * 4), ht(Tg, Tg + B), hg(np);
+  DevBuf<T> dp, dx, dt, dg;
+  dp.upload(hp, c.stream);
+  dx.upload(hx, c.stream);
+  dt.upload(ht, c.stream);
+  dg.alloc(np);
+  MlpActs<T> a;
+  mlp_forward<T>(dp.p, dx.p, B, a, c.stream);
+  const double loss = mlp_backward<T>(dp.p, dx.p, dt.p, B, a, dg.p, c.stream);
+  DMRG_CUDA(cudaMemcpyAsync(hg.data(), dg.p, sizeof(T) * np, cudaMemcpyDeviceToHost, c.stream));
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  for (int64_t i = 0; i < np; ++i) grad[i] = double(hg[i]);
+  return loss;
+}
+
+extern "C" int dmrg_mlp_loss_grad(dmrg_ctx* c, int32_t precision, const double* params,
+                                  const double* X, const double* Tg, int64_t B, double* loss,
+                                  double* grad) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(params && X && Tg && grad && B >= 1, DMRG_EINVAL, "bad arguments");
+    double l = precision == DMRG_FP64 ? loss_grad_t<double>(*c, params, X, Tg, B, grad)
+                                      : loss_grad_t<float>(*c, params, X, Tg, B, grad);
+    if (loss) *loss = l;
+  });
+}
+
+extern "C" int64_t dmrg_mlp_n_params(void) { return mlp_n_params(); }
 
 extern "C" int dmrg_heff_cost(dmrg_ctx* c, int32_t p, double* flops, double* bytes,
                               int64_t* n_items) {
