@@ -242,6 +242,26 @@ int dmrg_get_counters(dmrg_ctx* ctx, dmrg_counters* out);
  * plus wave function in and out, at the element size of the context's precision). */
 int dmrg_heff_cost(dmrg_ctx* ctx, int32_t p, double* flops, double* bytes, int64_t* n_items);
 
+/* Batch mode (not in the paper; many independent problems at once).  A batch groups
+ * contexts (1..64, same precision, blocks built).  dmrg_batch_sweep runs one sweep of
+ * every context in lockstep: at step j each context does its own j-th two-site step
+ * (position order as in dmrg_sweep; contexts with fewer steps drop out), and every
+ * Davidson iteration computes the H_eff products of all contexts still iterating in ONE
+ * fused kernel launch (tiles of all superblocks in one list), recorded once per step in a
+ * CUDA graph on an internal stream and replayed with new vector pointers.  Results are
+ * identical to sweeping the contexts one by one.  M: [n] kept states per context;
+ * energies: optional [n] energy of each context's last step. */
+typedef struct dmrg_batch dmrg_batch;
+typedef struct {
+  int64_t products;         /* batched product launches (graph replays included)        */
+  double heff_seconds;      /* device time of those products (CUDA events)             */
+  int64_t launches;         /* kernel launches issued by the library (graph nodes once) */
+} dmrg_batch_stats;
+int dmrg_batch_create(int32_t n, dmrg_ctx* const* ctx, dmrg_batch** out);
+int dmrg_batch_destroy(dmrg_batch* b);
+const char* dmrg_batch_last_error(const dmrg_batch* b);
+int dmrg_batch_sweep(dmrg_batch* b, const int32_t* M, double* energies, dmrg_batch_stats* st);
+
 #ifdef __cplusplus
 }
 #endif

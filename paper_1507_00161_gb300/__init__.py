@@ -27,7 +27,9 @@ EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
             "dmrg_set_options", "dmrg_get_counters", "dmrg_heff_cost",
             "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
-            "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params"]
+            "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params",
+            "dmrg_batch_create", "dmrg_batch_destroy", "dmrg_batch_last_error",
+            "dmrg_batch_sweep"]
 PRECOND_DIAG = 0
 PRECOND_MLP = 1
 
@@ -74,6 +76,11 @@ class StepStats(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("products", ctypes.c_int64), ("heff_seconds", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
 
 class Counters(ctypes.Structure):
@@ -128,6 +135,14 @@ def load_library(path: str = LIB_PATH):
     lib.dmrg_last_error.restype = ctypes.c_char_p
     lib.dmrg_mlp_n_params.argtypes = []
     lib.dmrg_mlp_n_params.restype = ctypes.c_int64
+    lib.dmrg_batch_create.argtypes = [i32, P, ctypes.POINTER(P)]
+    lib.dmrg_batch_create.restype = ctypes.c_int
+    lib.dmrg_batch_destroy.argtypes = [P]
+    lib.dmrg_batch_destroy.restype = ctypes.c_int
+    lib.dmrg_batch_last_error.argtypes = [P]
+    lib.dmrg_batch_last_error.restype = ctypes.c_char_p
+    lib.dmrg_batch_sweep.argtypes = [P, P, P, ctypes.POINTER(BatchStats)]
+    lib.dmrg_batch_sweep.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -316,3 +331,41 @@ class DMRG:
         self._check(self.lib.dmrg_heff_cost(self.h, p, ctypes.byref(f), ctypes.byref(b),
                                             ctypes.byref(n)))
         return f.value, b.value, n.value
+
+
+class Batch:
+    """Several contexts swept in lockstep with one fused H_eff launch per Davidson
+    iteration (dmrg_batch_* in include/dmrg.h).  The contexts must outlive the batch."""
+
+    def __init__(self, contexts):
+        self.lib = load_library()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[d.h for d in self.contexts])
+        h = ctypes.c_void_p()
+        rc = self.lib.dmrg_batch_create(len(self.contexts), arr, ctypes.byref(h))
+        self.h = h.value
+        if rc != DMRG_OK:
+            msg = self.lib.dmrg_batch_last_error(self.h).decode() if self.h else "create failed"
+            self.close()
+            raise DmrgError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dmrg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, M):
+        n = len(self.contexts)
+        Ms = np.ascontiguousarray(np.broadcast_to(np.asarray(M, dtype=np.int32), (n,)))
+        e = np.zeros(n)
+        st = BatchStats()
+        rc = self.lib.dmrg_batch_sweep(self.h, _np_ptr(Ms), _np_ptr(e), ctypes.byref(st))
+        if rc != DMRG_OK:
+            raise DmrgError(rc, self.lib.dmrg_batch_last_error(self.h).decode())
+        return e, {f: getattr(st, f) for f, _ in BatchStats._fields_}

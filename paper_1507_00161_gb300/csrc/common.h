@@ -368,26 +368,46 @@ struct HeffTile {
   int32_t ld;                 // dRo of the output block
   int32_t r0, c0, m, n;
   int32_t i0, i1;             // items [i0, i1)
-  int32_t pad;
+  int32_t inst;               // instance (batch mode), 0 for one context
 };
 // deterministic sum of the partial tiles of one output tile
 struct HeffRed {
   int64_t yoff, poff;
   int32_t ld, r0, c0, m, n, groups;
+  int32_t inst, pad;
+};
+// base pointers of every instance of a fused launch (passed by value); active[inst] == 0
+// makes the thread blocks of that instance return at once (batch mode)
+constexpr int kMaxInst = 64;
+template <class T>
+struct HeffPtrs {
+  const T* L[kMaxInst];
+  const T* R[kMaxInst];
+  const T* X[kMaxInst];
+  T* Y[kMaxInst];
+  T* P[kMaxInst];
+  const int32_t* active;
 };
 template <class T>
-void heff_reduce(const HeffRed* d_red, int64_t n_red, const T* partial, T* Y, cudaStream_t s);
+void heff_reduce(const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s);
 // mixed path: the same product with 3xTF32 warp MMAs (heff_tc.cu)
 void heff_tc(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
-             const HeffRed* d_red, int64_t n_red, const float* L, const float* R, const float* X,
-             float* Y, float* partial, cudaStream_t s);
+             const HeffRed* d_red, int64_t n_red, const HeffPtrs<float>& ptrs, cudaStream_t s);
 template <class TO>
 void pad_psi(const double* x, TO* xp, const int64_t* src_off, const int64_t* dst_off,
              const int32_t* len, int nblocks, cudaStream_t s);
 template <class T>
 void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
-                const HeffRed* d_red, int64_t n_red, const T* L, const T* R, const T* X, T* Y,
-                T* partial, cudaStream_t s);
+                const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s);
+// psi into / out of the 16-byte aligned staging copies, with the vector pointers read from
+// device memory (*xp_ptr, *out_ptr) so that a captured graph can be replayed on new vectors
+template <class TO>
+void pad_psi_ind(const double* const* x_ptr, TO* xp, const int64_t* src_off,
+                 const int64_t* dst_off, const int32_t* len, int nblocks, const int32_t* active,
+                 cudaStream_t s);
+template <class TI>
+void out_to_f64_ind(const TI* y, double* const* out_ptr, int64_t n, const int32_t* active,
+                    cudaStream_t s);
 
 // enlargement of block operators by one site (kernels.cu)
 struct EntryDev {

@@ -126,6 +126,10 @@ struct Super {
   DevBuf<HeffTile> ftiles;
   DevBuf<HeffRed> fred;
   int64_t n_ftiles = 0, n_fred = 0, p_elems = 0;
+  std::vector<HeffItem> h_items;
+  std::vector<HeffTile> h_tiles;
+  std::vector<HeffRed> h_red;
+  std::vector<double> h_cost;
   // 16-byte aligned copy of psi used by the fused product
   std::vector<int64_t> pad_off;
   int64_t pad_size = 0;
@@ -170,7 +174,7 @@ struct dmrg_ctx {
   // scratch
   dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
   dmrg::DevBuf<float> f32a, f32b, f32T, part32;
-  dmrg::DevBuf<double> part64, xpad64;
+  dmrg::DevBuf<double> part64, xpad64, ybat64;
   dmrg::DevBuf<float> xpad32;
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
@@ -629,7 +633,7 @@ static void build_super(Ctx& c, int p) {
           t.c0 = c0;
           t.m = std::min(32, dLo - r0);
           t.n = std::min(32, dRo - c0);
-          t.pad = 0;
+          t.inst = 0;
           const int64_t mn = int64_t(t.m) * t.n;
           if (groups > 1) {
             HeffRed rd;
@@ -641,6 +645,8 @@ static void build_super(Ctx& c, int p) {
             rd.m = t.m;
             rd.n = t.n;
             rd.groups = groups;
+            rd.inst = 0;
+            rd.pad = 0;
             fr.push_back(rd);
           }
           for (int g = 0; g < groups; ++g) {
@@ -707,6 +713,12 @@ static void build_super(Ctx& c, int p) {
     sb->fitems.upload(fi, c.stream);
     sb->ftiles.upload(tl, c.stream);
     sb->fred.upload(fr, c.stream);
+    // host copies for batch mode (lists of several instances in one launch)
+    sb->h_items = fi;
+    sb->h_tiles = tl;
+    sb->h_red = fr;
+    sb->h_cost.resize(ft.size());
+    for (size_t i = 0; i < ft.size(); ++i) sb->h_cost[i] = ft[i].cost;
     sb->n_ftiles = int64_t(tl.size());
     sb->n_fred = int64_t(fr.size());
     sb->p_elems = pelems;
@@ -794,15 +806,26 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y) {
     c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad64.alloc(sb.pad_size);
     pad_psi<double>(x, c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
-    heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, sb.L.data.p,
-                       sb.R.data.p, c.xpad64.p, y, c.part64.p, c.stream);
+    HeffPtrs<double> ptr{};
+    ptr.L[0] = sb.L.data.p;
+    ptr.R[0] = sb.R.data.p;
+    ptr.X[0] = c.xpad64.p;
+    ptr.Y[0] = y;
+    ptr.P[0] = c.part64.p;
+    heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr,
+                       c.stream);
   } else {
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
     c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad32.alloc(sb.pad_size);
     pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
-    heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, sb.L.data32.p,
-            sb.R.data32.p, c.xpad32.p, c.f32b.p, c.part32.p, c.stream);
+    HeffPtrs<float> ptr{};
+    ptr.L[0] = sb.L.data32.p;
+    ptr.R[0] = sb.R.data32.p;
+    ptr.X[0] = c.xpad32.p;
+    ptr.Y[0] = c.f32b.p;
+    ptr.P[0] = c.part32.p;
+    heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, c.stream);
     to_f64(c.f32b.p, y, sb.size, c.stream);
   }
 }
@@ -940,130 +963,184 @@ struct DavResult {
   double heff_seconds = 0;
 };
 
-static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
-  PhaseTimer tm(c.t_davidson);
-  const int64_t n = sb.size;
-  const int sub = std::max(4, std::min(64, c.opt.dav_max_sub));
-  ensure_ws(c, n, sub);
+// Davidson as a resumable run: dav_begin prepares the first vector, every H_eff product
+// is requested through (px -> py), dav_after_product consumes it and either requests the
+// next product or finishes.  davidson() drives one run; batch mode drives several runs
+// with one fused product launch per iteration.
+struct DavRun {
+  Super* sb = nullptr;
+  int64_t n = 0, ld = 0;
+  int sub = 0, k = 0, nprod = 0, nhist = 0;
+  bool use_mlp = false, done = false;
+  DavResult res;
+  double* out = nullptr;
+  double* px = nullptr;   // pending product: py = H_eff px
+  double* py = nullptr;
+};
+
+static const int kHist = 8;
+
+struct DavPtrs {
+  double *Hs, *w, *Y, *scr, *sc, *part;
+  const double* const* Vp;
+  const double* const* AVp;
+  DavPtrs(Ctx& c, int sub) {
+    Hs = c.small.p;              // 64 x 64, row k holds <v_i, H v_k>, i <= k
+    w = Hs + 64 * 64;            // Ritz values, ascending
+    Y = w + 64;                  // 64 x 64, row j = coefficients of the j-th Ritz vector
+    scr = Y + 64 * 64;           // 2 x 64 x 64 scratch for the Ritz solve
+    sc = scr + 2 * 64 * 64;      // device scalars
+    part = c.partials.p;
+    Vp = c.vptr.p;
+    AVp = c.vptr.p + sub;
+  }
+};
+
+static void dav_readback(Ctx& c, const double* d, int cnt, double* h) {
+  DMRG_CUDA(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.stream));
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+}
+static void dav_d2d(Ctx& c, double* dst, const double* src, int64_t n) {
+  DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
+}
+
+static void dav_begin(Ctx& c, Super& sb, const double* guess, double* out, DavRun& R) {
+  R = DavRun();
+  R.sb = &sb;
+  R.n = sb.size;
+  R.sub = std::max(4, std::min(64, c.opt.dav_max_sub));
+  R.out = out;
+  ensure_ws(c, R.n, R.sub);
   ensure_diag(c, sb);
-  cudaStream_t s = c.stream;
-  double* Hs = c.small.p;               // 64 x 64, row k holds <v_i, H v_k>, i <= k
-  double* w = Hs + 64 * 64;             // Ritz values, ascending
-  double* Y = w + 64;                   // 64 x 64, row j = coefficients of the j-th Ritz vector
-  double* scr = Y + 64 * 64;            // 2 x 64 x 64 scratch for the Ritz solve
-  double* sc = scr + 2 * 64 * 64;       // device scalars
-  double* part = c.partials.p;
-  const double* const* Vp = c.vptr.p;
-  const double* const* AVp = c.vptr.p + sub;
-  const int64_t ld = c.ws_n;
-  auto vec = [&](int j) { return c.V.p + j * ld; };
-  auto avec = [&](int j) { return c.AV.p + j * ld; };
-  auto readback = [&](const double* d, int cnt, double* h) {
-    DMRG_CUDA(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
-    DMRG_CUDA(cudaStreamSynchronize(s));
-  };
-  auto d2d = [&](double* dst, const double* src) {
-    DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  };
-  const int kHist = 8;
-  int nhist = 0;
-  const bool use_mlp = c.opt.reserved0 == DMRG_PRECOND_MLP && c.mlp_trained;
+  R.ld = c.ws_n;
+  R.use_mlp = c.opt.reserved0 == DMRG_PRECOND_MLP && c.mlp_trained;
   if (c.mlp_harvest) {
-    c.hist_x.alloc(kHist * ld);
-    c.hist_r.alloc(kHist * ld);
+    c.hist_x.alloc(kHist * R.ld);
+    c.hist_r.alloc(kHist * R.ld);
     c.hist_theta.alloc(kHist);
-    c.hist_tmp.alloc(ld);
+    c.hist_tmp.alloc(R.ld);
   }
   c.mlp_sc.alloc(64);
-  // v_0 = x0 / |x0|
-  d2d(vec(0), guess);
-  dot(vec(0), vec(0), n, sc, part, s);
-  scale_vec(vec(0), n, sc, 1, s);
-  heff_timed(c, sb, vec(0), avec(0));
-  int nprod = 1, k = 1;
-  multidot(Vp, 1, avec(0), n, Hs, part, s);
-  DavResult res;
-  const double tol = c.opt.dav_tol;
-  double h[4];
-  while (true) {
-    // Ritz pair of the projected matrix, residual r = H x - theta x
-    ritz_solve(Hs, 64, k, scr, w, Y, s);
-    lincomb(Vp, Y, k, n, c.x.p, 0.0, 1.0, s);
-    lincomb(AVp, Y, k, n, c.Ax.p, 0.0, 1.0, s);
-    davidson_residual(c.x.p, c.Ax.p, w, n, c.r.p, s);
-    dot(c.r.p, c.r.p, n, sc + 1, part, s);
-    DMRG_CUDA(cudaMemcpyAsync(sc, w, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    readback(sc, 2, h);
-    const double theta = h[0], rn = std::sqrt(std::max(h[1], 0.0));
-    res.theta = theta;
-    res.resid = rn;
-    res.nprod = nprod;
-    if (c.mlp_harvest && nhist < kHist) {   // iterate, residual and Ritz value for training
-      d2d(c.hist_x.p + nhist * ld, c.x.p);
-      d2d(c.hist_r.p + nhist * ld, c.r.p);
-      DMRG_CUDA(cudaMemcpyAsync(c.hist_theta.p + nhist, w, sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
-      ++nhist;
-    }
-    // FP32 products cannot resolve residuals below ~1e-7 of |H|: relative floor
-    const double tol_eff =
-        c.opt.precision == DMRG_FP64 ? tol : std::max(tol, 1e-6 * std::max(1.0, std::fabs(theta)));
-    if (rn <= tol_eff || nprod >= c.opt.dav_max_iter) {
-      res.converged = rn <= tol_eff;
-      break;
-    }
-    // correction: t = r / (theta - D), clamped (diagonal), or the learned map
-    davidson_correction(c.r.p, sb.diag.p, w, n, c.t.p, s);
-    if (use_mlp) {
-      double* fs = c.mlp_sc.p + 8;
-      DMRG_CUDA(cudaMemcpyAsync(fs, w, sizeof(double), cudaMemcpyDeviceToDevice, s));
-      dot(c.r.p, c.r.p, n, fs + 1, part, s);
-      dot(c.t.p, c.t.p, n, fs + 2, part, s);
-      c.mlp_feat.alloc(n * 4);
-      mlp_features<float>(c.r.p, c.x.p, sb.diag.p, fs, n, c.mlp_feat.p, s);
-      mlp_forward<float>(c.mlp_p.p, c.mlp_feat.p, n, c.mlp_acts, s);
-      mlp_output_to_double<float>(c.mlp_acts.Y.p, c.t.p, n, s);
-    }
-    if (k >= sub) {   // thick restart from the two lowest Ritz vectors
-      lincomb(Vp, Y + 64, k, n, c.x1.p, 0.0, 1.0, s);
-      lincomb(AVp, Y + 64, k, n, c.Ax1.p, 0.0, 1.0, s);
-      d2d(vec(0), c.x.p);
-      d2d(vec(1), c.x1.p);
-      d2d(avec(0), c.Ax.p);
-      d2d(avec(1), c.Ax1.p);
-      k_set_hs_diag<<<1, 32, 0, s>>>(Hs, 64, w);
-      DMRG_LAUNCHED();
-      k = 2;
-    }
-    dot(c.t.p, c.t.p, n, sc + 2, part, s);
-    for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
-      multidot(Vp, k, c.t.p, n, sc + 32, part, s);
-      lincomb(Vp, sc + 32, k, n, c.t.p, 1.0, -1.0, s);
-    }
-    dot(c.t.p, c.t.p, n, sc + 3, part, s);
-    readback(sc + 2, 2, h);
-    const double tn0 = std::sqrt(std::max(h[0], 0.0)), tn = std::sqrt(std::max(h[1], 0.0));
-    if (tn <= 1e-14 * std::max(tn0, 1e-300)) break;   // no new direction left
-    d2d(vec(k), c.t.p);
-    scale_vec(vec(k), n, sc + 3, 1, s);
-    heff_timed(c, sb, vec(k), avec(k));
-    ++nprod;
-    multidot(Vp, k + 1, avec(k), n, Hs + 64 * k, part, s);
-    ++k;
-  }
-  dot(c.x.p, c.x.p, n, sc + 4, part, s);
-  scale_vec(c.x.p, n, sc + 4, 1, s);
+  DavPtrs P(c, R.sub);
+  double* v0 = c.V.p;
+  dav_d2d(c, v0, guess, R.n);
+  dot(v0, v0, R.n, P.sc, P.part, c.stream);
+  scale_vec(v0, R.n, P.sc, 1, c.stream);
+  R.px = v0;
+  R.py = c.AV.p;
+}
+
+static void dav_finish(Ctx& c, DavRun& R) {
+  Super& sb = *R.sb;
+  DavPtrs P(c, R.sub);
+  const int64_t n = R.n;
+  double h[2];
+  dot(c.x.p, c.x.p, n, P.sc + 4, P.part, c.stream);
+  scale_vec(c.x.p, n, P.sc + 4, 1, c.stream);
   if (c.opt.precision != DMRG_FP64) {
     // energy of the mixed path: FP64 Rayleigh quotient of the converged vector
     heff64(c, sb, c.x.p, c.Ax.p);
-    dot(c.x.p, c.Ax.p, n, sc + 5, part, s);
-    readback(sc + 5, 1, h);
-    res.theta = h[0];
+    dot(c.x.p, c.Ax.p, n, P.sc + 5, P.part, c.stream);
+    dav_readback(c, P.sc + 5, 1, h);
+    R.res.theta = h[0];
   }
-  d2d(out, c.x.p);
-  if (c.mlp_harvest && nhist > 0) harvest(c, sb, nhist, c.x.p);
-  res.heff_seconds = resolve_heff_timing(c);
-  return res;
+  dav_d2d(c, R.out, c.x.p, n);
+  if (c.mlp_harvest && R.nhist > 0) harvest(c, sb, R.nhist, c.x.p);
+  R.done = true;
+  R.px = R.py = nullptr;
+}
+
+// consume the product of vector k (py = H v_k), then either finish or request the next
+static void dav_after_product(Ctx& c, DavRun& R) {
+  Super& sb = *R.sb;
+  cudaStream_t s = c.stream;
+  DavPtrs P(c, R.sub);
+  const int64_t n = R.n, ld = R.ld;
+  auto vec = [&](int j) { return c.V.p + j * ld; };
+  auto avec = [&](int j) { return c.AV.p + j * ld; };
+  multidot(P.Vp, R.k + 1, avec(R.k), n, P.Hs + 64 * R.k, P.part, s);
+  ++R.k;
+  ++R.nprod;
+  const double tol = c.opt.dav_tol;
+  double h[4];
+  // Ritz pair of the projected matrix, residual r = H x - theta x
+  ritz_solve(P.Hs, 64, R.k, P.scr, P.w, P.Y, s);
+  lincomb(P.Vp, P.Y, R.k, n, c.x.p, 0.0, 1.0, s);
+  lincomb(P.AVp, P.Y, R.k, n, c.Ax.p, 0.0, 1.0, s);
+  davidson_residual(c.x.p, c.Ax.p, P.w, n, c.r.p, s);
+  dot(c.r.p, c.r.p, n, P.sc + 1, P.part, s);
+  DMRG_CUDA(cudaMemcpyAsync(P.sc, P.w, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  dav_readback(c, P.sc, 2, h);
+  const double theta = h[0], rn = std::sqrt(std::max(h[1], 0.0));
+  R.res.theta = theta;
+  R.res.resid = rn;
+  R.res.nprod = R.nprod;
+  if (c.mlp_harvest && R.nhist < kHist) {   // iterate, residual and Ritz value for training
+    dav_d2d(c, c.hist_x.p + R.nhist * ld, c.x.p, n);
+    dav_d2d(c, c.hist_r.p + R.nhist * ld, c.r.p, n);
+    DMRG_CUDA(cudaMemcpyAsync(c.hist_theta.p + R.nhist, P.w, sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    ++R.nhist;
+  }
+  // FP32 products cannot resolve residuals below ~1e-7 of |H|: relative floor
+  const double tol_eff =
+      c.opt.precision == DMRG_FP64 ? tol : std::max(tol, 1e-6 * std::max(1.0, std::fabs(theta)));
+  if (rn <= tol_eff || R.nprod >= c.opt.dav_max_iter) {
+    R.res.converged = rn <= tol_eff;
+    dav_finish(c, R);
+    return;
+  }
+  // correction: t = r / (theta - D), clamped (diagonal), or the learned map
+  davidson_correction(c.r.p, sb.diag.p, P.w, n, c.t.p, s);
+  if (R.use_mlp) {
+    double* fs = c.mlp_sc.p + 8;
+    DMRG_CUDA(cudaMemcpyAsync(fs, P.w, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    dot(c.r.p, c.r.p, n, fs + 1, P.part, s);
+    dot(c.t.p, c.t.p, n, fs + 2, P.part, s);
+    c.mlp_feat.alloc(n * 4);
+    mlp_features<float>(c.r.p, c.x.p, sb.diag.p, fs, n, c.mlp_feat.p, s);
+    mlp_forward<float>(c.mlp_p.p, c.mlp_feat.p, n, c.mlp_acts, s);
+    mlp_output_to_double<float>(c.mlp_acts.Y.p, c.t.p, n, s);
+  }
+  if (R.k >= R.sub) {   // thick restart from the two lowest Ritz vectors
+    lincomb(P.Vp, P.Y + 64, R.k, n, c.x1.p, 0.0, 1.0, s);
+    lincomb(P.AVp, P.Y + 64, R.k, n, c.Ax1.p, 0.0, 1.0, s);
+    dav_d2d(c, vec(0), c.x.p, n);
+    dav_d2d(c, vec(1), c.x1.p, n);
+    dav_d2d(c, avec(0), c.Ax.p, n);
+    dav_d2d(c, avec(1), c.Ax1.p, n);
+    k_set_hs_diag<<<1, 32, 0, s>>>(P.Hs, 64, P.w);
+    DMRG_LAUNCHED();
+    R.k = 2;
+  }
+  dot(c.t.p, c.t.p, n, P.sc + 2, P.part, s);
+  for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+    multidot(P.Vp, R.k, c.t.p, n, P.sc + 32, P.part, s);
+    lincomb(P.Vp, P.sc + 32, R.k, n, c.t.p, 1.0, -1.0, s);
+  }
+  dot(c.t.p, c.t.p, n, P.sc + 3, P.part, s);
+  dav_readback(c, P.sc + 2, 2, h);
+  const double tn0 = std::sqrt(std::max(h[0], 0.0)), tn = std::sqrt(std::max(h[1], 0.0));
+  if (tn <= 1e-14 * std::max(tn0, 1e-300)) {   // no new direction left
+    dav_finish(c, R);
+    return;
+  }
+  dav_d2d(c, vec(R.k), c.t.p, n);
+  scale_vec(vec(R.k), n, P.sc + 3, 1, s);
+  R.px = vec(R.k);
+  R.py = avec(R.k);
+}
+
+static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
+  PhaseTimer tm(c.t_davidson);
+  DavRun R;
+  dav_begin(c, sb, guess, out, R);
+  while (!R.done) {
+    heff_timed(c, sb, R.px, R.py);
+    dav_after_product(c, R);
+  }
+  R.res.heff_seconds = resolve_heff_timing(c);
+  return R.res;
 }
 
 
@@ -1844,5 +1921,357 @@ extern "C" int dmrg_heff_cost(dmrg_ctx* c, int32_t p, double* flops, double* byt
     if (flops) *flops = sb.flops;
     if (bytes) *bytes = sb.bytes;
     if (n_items) *n_items = sb.n_items;
+  });
+}
+
+// =======================================================================================
+// batch mode: several independent problems, one fused H_eff launch per Davidson iteration
+// =======================================================================================
+struct dmrg_batch {
+  std::string err = "no error";
+  std::vector<dmrg_ctx*> ctx;
+  int precision = DMRG_FP64;
+  cudaStream_t bs = nullptr;                 // internal stream (graph capture)
+  cudaEvent_t ev = nullptr;
+  std::vector<cudaEvent_t> ev_ctx;
+  // combined lists of the current step
+  dmrg::DevBuf<dmrg::HeffItem> items;
+  dmrg::DevBuf<dmrg::HeffTile> tiles;
+  dmrg::DevBuf<dmrg::HeffRed> red;
+  int64_t n_tiles = 0, n_red = 0;
+  // per-iteration tables: input and output vector pointers, active flags
+  struct Tab {
+    const double* in[dmrg::kMaxInst];
+    double* out[dmrg::kMaxInst];
+    int32_t active[dmrg::kMaxInst];
+  };
+  Tab* h_tab = nullptr;                      // pinned
+  Tab* d_tab = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int iter = 0;
+  // counters
+  int64_t products = 0, launches0 = 0;
+  double heff_seconds = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  ~dmrg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (h_tab) cudaFreeHost(h_tab);
+    if (d_tab) cudaFree(d_tab);
+    if (ev) cudaEventDestroy(ev);
+    for (auto e : ev_ctx) cudaEventDestroy(e);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (bs) cudaStreamDestroy(bs);
+  }
+};
+
+namespace dmrg {
+
+struct PoolScope {
+  Pool* prev;
+  explicit PoolScope(Pool* p) : prev(tl_pool) { tl_pool = p; }
+  ~PoolScope() { tl_pool = prev; }
+};
+
+// concatenate the fused lists of the instances' current superblocks (heaviest tiles first)
+static void batch_lists(dmrg_batch& B, const std::vector<int>& inst) {
+  std::vector<HeffItem> fi;
+  std::vector<std::pair<double, HeffTile>> ft;
+  std::vector<HeffRed> fr;
+  for (int i : inst) {
+    Super& sb = *B.ctx[i]->sb;
+    const int base = int(fi.size());
+    fi.insert(fi.end(), sb.h_items.begin(), sb.h_items.end());
+    for (size_t t = 0; t < sb.h_tiles.size(); ++t) {
+      HeffTile x = sb.h_tiles[t];
+      x.i0 += base;
+      x.i1 += base;
+      x.inst = i;
+      ft.push_back({sb.h_cost[t], x});
+    }
+    for (HeffRed r : sb.h_red) {
+      r.inst = i;
+      fr.push_back(r);
+    }
+  }
+  std::stable_sort(ft.begin(), ft.end(),
+                   [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<HeffTile> tl(ft.size());
+  for (size_t t = 0; t < ft.size(); ++t) tl[t] = ft[t].second;
+  B.items.upload(fi, B.bs);
+  B.tiles.upload(tl, B.bs);
+  B.red.upload(fr, B.bs);
+  B.n_tiles = int64_t(tl.size());
+  B.n_red = int64_t(fr.size());
+  DMRG_CUDA(cudaStreamSynchronize(B.bs));
+}
+
+// the product sequence of one batched iteration on the internal stream: psi of every
+// instance into its staging copy, one fused launch, one reduction, results out
+static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
+  const int32_t* act = B.d_tab->active;
+  if (B.precision == DMRG_FP64) {
+    HeffPtrs<double> ptr{};
+    ptr.active = act;
+    for (int i : inst) {
+      Ctx& c = *B.ctx[i];
+      Super& sb = *c.sb;
+      pad_psi_ind<double>(&B.d_tab->in[i], c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p,
+                          sb.d_pad_len.p, int(sb.bL.size()), act + i, B.bs);
+      ptr.L[i] = sb.L.data.p;
+      ptr.R[i] = sb.R.data.p;
+      ptr.X[i] = c.xpad64.p;
+      ptr.Y[i] = c.ybat64.p;
+      ptr.P[i] = c.part64.p;
+    }
+    heff_fused<double>(B.tiles.p, B.n_tiles, B.items.p, B.red.p, B.n_red, ptr, B.bs);
+    for (int i : inst) {
+      Ctx& c = *B.ctx[i];
+      out_to_f64_ind<double>(c.ybat64.p, &B.d_tab->out[i], c.sb->size, act + i, B.bs);
+    }
+  } else {
+    HeffPtrs<float> ptr{};
+    ptr.active = act;
+    for (int i : inst) {
+      Ctx& c = *B.ctx[i];
+      Super& sb = *c.sb;
+      pad_psi_ind<float>(&B.d_tab->in[i], c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p,
+                         sb.d_pad_len.p, int(sb.bL.size()), act + i, B.bs);
+      ptr.L[i] = sb.L.data32.p;
+      ptr.R[i] = sb.R.data32.p;
+      ptr.X[i] = c.xpad32.p;
+      ptr.Y[i] = c.f32b.p;
+      ptr.P[i] = c.part32.p;
+    }
+    heff_tc(B.tiles.p, B.n_tiles, B.items.p, B.red.p, B.n_red, ptr, B.bs);
+    for (int i : inst) {
+      Ctx& c = *B.ctx[i];
+      out_to_f64_ind<float>(c.f32b.p, &B.d_tab->out[i], c.sb->size, act + i, B.bs);
+    }
+  }
+}
+
+// staging buffers of every instance sized for its current superblock (before any capture)
+static void batch_buffers(dmrg_batch& B, const std::vector<int>& inst) {
+  for (int i : inst) {
+    Ctx& c = *B.ctx[i];
+    PoolScope ps(&c.pool);
+    Super& sb = *c.sb;
+    if (B.precision == DMRG_FP64) {
+      c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
+      c.xpad64.alloc(sb.pad_size);
+      c.ybat64.alloc(std::max<int64_t>(sb.size, 1));
+    } else {
+      c.f32b.alloc(std::max<int64_t>(sb.size, 1));
+      c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
+      c.xpad32.alloc(sb.pad_size);
+    }
+  }
+}
+
+// one batched product: tables up, fused sequence (eager on the first iteration of a step,
+// then captured once into a CUDA graph and replayed), ordering with every context stream
+static void batch_product(dmrg_batch& B, const std::vector<int>& inst, std::vector<DavRun>& runs) {
+  for (int k = 0; k < kMaxInst; ++k) B.h_tab->active[k] = 0;
+  for (int i : inst) {
+    B.h_tab->in[i] = runs[i].done ? nullptr : runs[i].px;
+    B.h_tab->out[i] = runs[i].done ? nullptr : runs[i].py;
+    B.h_tab->active[i] = runs[i].done ? 0 : 1;
+  }
+  for (int i : inst) {
+    DMRG_CUDA(cudaEventRecord(B.ev_ctx[i], B.ctx[i]->stream));
+    DMRG_CUDA(cudaStreamWaitEvent(B.bs, B.ev_ctx[i], 0));
+  }
+  DMRG_CUDA(cudaMemcpyAsync(B.d_tab, B.h_tab, sizeof(dmrg_batch::Tab), cudaMemcpyHostToDevice,
+                            B.bs));
+  DMRG_CUDA(cudaEventRecord(B.t0, B.bs));
+  if (B.iter == 0) {
+    batch_issue(B, inst);
+  } else {
+    if (!B.exec) {
+      cudaGraph_t g = nullptr;
+      DMRG_CUDA(cudaStreamBeginCapture(B.bs, cudaStreamCaptureModeThreadLocal));
+      try {
+        batch_issue(B, inst);
+      } catch (...) {
+        cudaStreamEndCapture(B.bs, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      DMRG_CUDA(cudaStreamEndCapture(B.bs, &g));
+      cudaError_t e = cudaGraphInstantiate(&B.exec, g, 0);
+      cudaGraphDestroy(g);
+      DMRG_CUDA(e);
+    }
+    DMRG_CUDA(cudaGraphLaunch(B.exec, B.bs));
+  }
+  DMRG_CUDA(cudaEventRecord(B.t1, B.bs));
+  DMRG_CUDA(cudaEventRecord(B.ev, B.bs));
+  for (int i : inst) DMRG_CUDA(cudaStreamWaitEvent(B.ctx[i]->stream, B.ev, 0));
+  DMRG_CUDA(cudaEventSynchronize(B.t1));
+  float ms = 0;
+  DMRG_CUDA(cudaEventElapsedTime(&ms, B.t0, B.t1));
+  B.heff_seconds += ms * 1e-3;
+  ++B.iter;
+  ++B.products;
+}
+
+struct BWork {
+  int inst, p, dir, M;
+};
+
+static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
+                       std::vector<dmrg_step_stats>& st) {
+  std::vector<int> inst;
+  std::vector<DavRun> runs(B.ctx.size());
+  std::vector<double> t0(B.ctx.size());
+  for (const BWork& w : work) {
+    Ctx& c = *B.ctx[w.inst];
+    PoolScope ps(&c.pool);
+    t0[w.inst] = now_s();
+    Super& sb = super_at(c, w.p);
+    c.psi_guess.alloc(std::max<int64_t>(sb.size, 1));
+    predict(c, sb, w.p, w.dir, c.psi_guess.p);
+    c.psi.alloc(std::max<int64_t>(sb.size, 1));
+    dav_begin(c, sb, c.psi_guess.p, c.psi.p, runs[w.inst]);
+    inst.push_back(w.inst);
+  }
+  batch_buffers(B, inst);
+  batch_lists(B, inst);
+  if (B.exec) {
+    cudaGraphExecDestroy(B.exec);
+    B.exec = nullptr;
+  }
+  B.iter = 0;
+  while (true) {
+    bool any = false;
+    for (int i : inst) any = any || !runs[i].done;
+    if (!any) break;
+    batch_product(B, inst, runs);
+    for (int i : inst) {
+      if (runs[i].done) continue;
+      PoolScope ps(&B.ctx[i]->pool);
+      dav_after_product(*B.ctx[i], runs[i]);
+    }
+  }
+  for (const BWork& w : work) {
+    Ctx& c = *B.ctx[w.inst];
+    PoolScope ps(&c.pool);
+    c.psi_valid = true;
+    c.psi_p = w.p;
+    const double flops = c.sb->flops, bytes = c.sb->bytes;
+    TruncResult tr = truncate_renormalize(c, w.p, w.dir, w.M);
+    dmrg_step_stats& s = st[w.inst];
+    s.p = w.p;
+    s.dir = w.dir;
+    s.n_products = runs[w.inst].res.nprod;
+    s.kept = tr.kept;
+    s.energy = runs[w.inst].res.theta;
+    s.residual = runs[w.inst].res.resid;
+    s.trunc_err = tr.trunc;
+    s.seconds = now_s() - t0[w.inst];
+    s.heff_seconds = 0;
+    s.heff_flops = flops;
+    s.heff_bytes = bytes;
+  }
+}
+
+}  // namespace dmrg
+
+template <class F>
+static int bguarded(dmrg_batch* b, F&& f) {
+  if (!b) return DMRG_EINVAL;
+  try {
+    f();
+    return DMRG_OK;
+  } catch (const Error& e) {
+    b->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    b->err = "host allocation failed";
+    return DMRG_ENOMEM;
+  } catch (const std::exception& e) {
+    b->err = e.what();
+    return DMRG_EINVAL;
+  }
+}
+
+extern "C" int dmrg_batch_create(int32_t n, dmrg_ctx* const* ctxs, dmrg_batch** out) {
+  if (!out) return DMRG_EINVAL;
+  *out = nullptr;
+  dmrg_batch* b = nullptr;
+  try {
+    b = new dmrg_batch();
+  } catch (...) {
+    return DMRG_ENOMEM;
+  }
+  int rc = bguarded(b, [&] {
+    DMRG_REQUIRE(n >= 1 && n <= kMaxInst && ctxs, DMRG_EINVAL, "batch size must be in [1, 64]");
+    for (int i = 0; i < n; ++i) {
+      DMRG_REQUIRE(ctxs[i] && ctxs[i]->N > 0, DMRG_EINVAL, "invalid context in batch");
+      for (int j = 0; j < i; ++j)
+        DMRG_REQUIRE(ctxs[i] != ctxs[j], DMRG_EINVAL, "a context appears twice in the batch");
+      b->ctx.push_back(ctxs[i]);
+    }
+    b->precision = ctxs[0]->opt.precision;
+    DMRG_CUDA(cudaStreamCreate(&b->bs));
+    DMRG_CUDA(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+    b->ev_ctx.resize(n);
+    for (int i = 0; i < n; ++i) DMRG_CUDA(cudaEventCreateWithFlags(&b->ev_ctx[i], cudaEventDisableTiming));
+    DMRG_CUDA(cudaEventCreate(&b->t0));
+    DMRG_CUDA(cudaEventCreate(&b->t1));
+    DMRG_CUDA(cudaMallocHost(&b->h_tab, sizeof(dmrg_batch::Tab)));
+    DMRG_CUDA(cudaMalloc(&b->d_tab, sizeof(dmrg_batch::Tab)));
+  });
+  *out = b;
+  return rc;
+}
+
+extern "C" int dmrg_batch_destroy(dmrg_batch* b) {
+  delete b;
+  return DMRG_OK;
+}
+
+extern "C" const char* dmrg_batch_last_error(const dmrg_batch* b) {
+  return b ? b->err.c_str() : "NULL batch";
+}
+
+extern "C" int dmrg_batch_sweep(dmrg_batch* b, const int32_t* M, double* energies,
+                                dmrg_batch_stats* st) {
+  return bguarded(b, [&] {
+    DMRG_REQUIRE(M != nullptr, DMRG_EINVAL, "M is NULL");
+    const int n = int(b->ctx.size());
+    for (int i = 0; i < n; ++i) {
+      DMRG_REQUIRE(b->ctx[i]->built, DMRG_EINVAL, "dmrg_build_blocks has not been called");
+      DMRG_REQUIRE(b->ctx[i]->opt.precision == b->precision, DMRG_EINVAL,
+                   "all contexts of a batch must use the same precision");
+      DMRG_REQUIRE(M[i] >= 1, DMRG_EINVAL, "M must be positive");
+    }
+    std::vector<std::vector<std::pair<int, int>>> seq(n);
+    size_t len = 0;
+    for (int i = 0; i < n; ++i) {
+      const int N = b->ctx[i]->N;
+      for (int p = 1; p <= N - 3; ++p) seq[i].push_back({p, 0});
+      for (int p = N - 3; p >= 1; --p) seq[i].push_back({p, 1});
+      len = std::max(len, seq[i].size());
+    }
+    const int64_t p0 = b->products;
+    const double h0 = b->heff_seconds;
+    const int64_t l0 = g_launches.load();
+    std::vector<dmrg_step_stats> last(n), cur(n);
+    for (size_t j = 0; j < len; ++j) {
+      std::vector<BWork> work;
+      for (int i = 0; i < n; ++i)
+        if (j < seq[i].size()) work.push_back(BWork{i, seq[i][j].first, seq[i][j].second, M[i]});
+      batch_step(*b, work, cur);
+      for (const BWork& w : work) last[w.inst] = cur[w.inst];
+    }
+    if (energies)
+      for (int i = 0; i < n; ++i) energies[i] = last[i].energy;
+    if (st) {
+      st->products = b->products - p0;
+      st->heff_seconds = b->heff_seconds - h0;
+      st->launches = g_launches.load() - l0;
+    }
   });
 }

@@ -65,8 +65,7 @@ __device__ __forceinline__ void stage(T* dst, const T* src, int elems, int lane)
 template <class T>
 __global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 4 : 2)
     k_heff_fused(const HeffTile* __restrict__ tiles, const HeffItem* __restrict__ items,
-                 const T* __restrict__ L, const T* __restrict__ R, const T* __restrict__ X,
-                 T* __restrict__ Y, T* __restrict__ P) {
+                 const HeffPtrs<T> ptrs) {
   constexpr int kRing = kRingBytes / int(sizeof(T));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* const base = reinterpret_cast<T*>(smem_raw);
@@ -75,6 +74,12 @@ __global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 4 : 2)
   T* const Xs = ring + kRing;
   __shared__ int slot_pos[kW][kDepth];
   const HeffTile t = tiles[blockIdx.x];
+  if (ptrs.active && !ptrs.active[t.inst]) return;   // whole block: uniform
+  const T* __restrict__ L = ptrs.L[t.inst];
+  const T* __restrict__ R = ptrs.R[t.inst];
+  const T* __restrict__ X = ptrs.X[t.inst];
+  T* __restrict__ Y = ptrs.Y[t.inst];
+  T* __restrict__ P = ptrs.P[t.inst];
   const int m = t.m, n = t.n;
   const int G = 32 / n;                // row groups
   const int c = lane % n, g = lane / n;
@@ -222,9 +227,11 @@ __global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 4 : 2)
 
 // psi' tile = sum over groups (in group order) of the partial tiles
 template <class T>
-__global__ void k_heff_reduce(const HeffRed* __restrict__ red, const T* __restrict__ P,
-                              T* __restrict__ Y) {
+__global__ void k_heff_reduce(const HeffRed* __restrict__ red, const HeffPtrs<T> ptrs) {
   const HeffRed r = red[blockIdx.x];
+  if (ptrs.active && !ptrs.active[r.inst]) return;
+  const T* __restrict__ P = ptrs.P[r.inst];
+  T* __restrict__ Y = ptrs.Y[r.inst];
   const int mn = r.m * r.n;
   for (int e = threadIdx.x; e < mn; e += blockDim.x) {
     T s = T(0);
@@ -246,18 +253,17 @@ __global__ void k_pad_psi(const TI* __restrict__ x, TO* __restrict__ xp,
 }
 
 template <class T>
-void heff_reduce(const HeffRed* d_red, int64_t n_red, const T* partial, T* Y, cudaStream_t s) {
+void heff_reduce(const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s) {
   if (n_red <= 0) return;
-  k_heff_reduce<T><<<int(n_red), 128, 0, s>>>(d_red, partial, Y);
+  k_heff_reduce<T><<<int(n_red), 128, 0, s>>>(d_red, ptrs);
   DMRG_LAUNCHED();
 }
-template void heff_reduce<float>(const HeffRed*, int64_t, const float*, float*, cudaStream_t);
-template void heff_reduce<double>(const HeffRed*, int64_t, const double*, double*, cudaStream_t);
+template void heff_reduce<float>(const HeffRed*, int64_t, const HeffPtrs<float>&, cudaStream_t);
+template void heff_reduce<double>(const HeffRed*, int64_t, const HeffPtrs<double>&, cudaStream_t);
 
 template <class T>
 void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
-                const HeffRed* d_red, int64_t n_red, const T* L, const T* R, const T* X, T* Y,
-                T* partial, cudaStream_t s) {
+                const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s) {
   if (n_tiles <= 0) return;
   const size_t smem = sizeof(T) * kW * (kRingBytes / sizeof(T) + kXS);
   static bool attr_set = false;   // per process: the attribute belongs to the kernel
@@ -266,19 +272,61 @@ void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_item
                                    int(smem)));
     attr_set = true;
   }
-  k_heff_fused<T><<<int(n_tiles), kW * 32, smem, s>>>(d_tiles, d_items, L, R, X, Y, partial);
+  k_heff_fused<T><<<int(n_tiles), kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
   DMRG_LAUNCHED();
-  if (n_red > 0) {
-    k_heff_reduce<T><<<int(n_red), 128, 0, s>>>(d_red, partial, Y);
-    DMRG_LAUNCHED();
-  }
+  heff_reduce<T>(d_red, n_red, ptrs, s);
 }
 template void heff_fused<double>(const HeffTile*, int64_t, const HeffItem*, const HeffRed*,
-                                 int64_t, const double*, const double*, const double*, double*,
-                                 double*, cudaStream_t);
-template void heff_fused<float>(const HeffTile*, int64_t, const HeffItem*, const HeffRed*,
-                                int64_t, const float*, const float*, const float*, float*,
-                                float*, cudaStream_t);
+                                 int64_t, const HeffPtrs<double>&, cudaStream_t);
+
+// staging with the vector pointer read from device memory (graph replay on new vectors)
+template <class TO>
+__global__ void k_pad_psi_ind(const double* const* __restrict__ xptr, TO* __restrict__ xp,
+                              const int64_t* __restrict__ src_off,
+                              const int64_t* __restrict__ dst_off,
+                              const int32_t* __restrict__ len, const int32_t* __restrict__ active) {
+  if (active && !active[0]) return;
+  const int b = blockIdx.x;
+  const double* s = xptr[0] + src_off[b];
+  TO* d = xp + dst_off[b];
+  for (int i = threadIdx.x; i < len[b]; i += blockDim.x) d[i] = TO(s[i]);
+}
+
+template <class TI>
+__global__ void k_out_to_f64_ind(const TI* __restrict__ y, double* const* __restrict__ optr,
+                                 int64_t n, const int32_t* __restrict__ active) {
+  if (active && !active[0]) return;
+  double* o = optr[0];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    o[i] = double(y[i]);
+}
+
+template <class TO>
+void pad_psi_ind(const double* const* x_ptr, TO* xp, const int64_t* src_off,
+                 const int64_t* dst_off, const int32_t* len, int nblocks, const int32_t* active,
+                 cudaStream_t s) {
+  if (nblocks <= 0) return;
+  k_pad_psi_ind<TO><<<nblocks, 128, 0, s>>>(x_ptr, xp, src_off, dst_off, len, active);
+  DMRG_LAUNCHED();
+}
+template void pad_psi_ind<float>(const double* const*, float*, const int64_t*, const int64_t*,
+                                 const int32_t*, int, const int32_t*, cudaStream_t);
+template void pad_psi_ind<double>(const double* const*, double*, const int64_t*, const int64_t*,
+                                  const int32_t*, int, const int32_t*, cudaStream_t);
+
+template <class TI>
+void out_to_f64_ind(const TI* y, double* const* out_ptr, int64_t n, const int32_t* active,
+                    cudaStream_t s) {
+  if (n <= 0) return;
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
+  k_out_to_f64_ind<TI><<<blocks, 256, 0, s>>>(y, out_ptr, n, active);
+  DMRG_LAUNCHED();
+}
+template void out_to_f64_ind<float>(const float*, double* const*, int64_t, const int32_t*,
+                                    cudaStream_t);
+template void out_to_f64_ind<double>(const double*, double* const*, int64_t, const int32_t*,
+                                     cudaStream_t);
 
 template <class TO>
 void pad_psi(const double* x, TO* xp, const int64_t* src_off, const int64_t* dst_off,

@@ -161,12 +161,17 @@ __device__ __forceinline__ void stage2(float (&acc)[2][4][4], const float* Ls, i
 
 __global__ void __launch_bounds__(kW * 32, 3)
     k_heff_tc(const HeffTile* __restrict__ tiles, const HeffItem* __restrict__ items,
-              const float* __restrict__ L, const float* __restrict__ R,
-              const float* __restrict__ X, float* __restrict__ Y, float* __restrict__ P) {
+              const HeffPtrs<float> ptrs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* const base = reinterpret_cast<float*>(smem_raw);
   __shared__ int slot_pos[kW][kDepth];
   const HeffTile t = tiles[blockIdx.x];
+  if (ptrs.active && !ptrs.active[t.inst]) return;   // whole block: uniform
+  const float* __restrict__ L = ptrs.L[t.inst];
+  const float* __restrict__ R = ptrs.R[t.inst];
+  const float* __restrict__ X = ptrs.X[t.inst];
+  float* __restrict__ Y = ptrs.Y[t.inst];
+  float* __restrict__ P = ptrs.P[t.inst];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gid = lane >> 2, tig = lane & 3;
   float* const ring = base + warp * (kRing + kXS);
@@ -322,8 +327,7 @@ __global__ void __launch_bounds__(kW * 32, 3)
 }  // namespace tc
 
 void heff_tc(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
-             const HeffRed* d_red, int64_t n_red, const float* L, const float* R, const float* X,
-             float* Y, float* partial, cudaStream_t s) {
+             const HeffRed* d_red, int64_t n_red, const HeffPtrs<float>& ptrs, cudaStream_t s) {
   if (n_tiles <= 0) return;
   const size_t smem = sizeof(float) * tc::kW * (tc::kRing + tc::kXS);
   static bool attr_set = false;
@@ -332,9 +336,9 @@ void heff_tc(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
                                    int(smem)));
     attr_set = true;
   }
-  tc::k_heff_tc<<<int(n_tiles), tc::kW * 32, smem, s>>>(d_tiles, d_items, L, R, X, Y, partial);
+  tc::k_heff_tc<<<int(n_tiles), tc::kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
   DMRG_LAUNCHED();
-  heff_reduce<float>(d_red, n_red, partial, Y, s);
+  heff_reduce<float>(d_red, n_red, ptrs, s);
 }
 
 }  // namespace dmrg

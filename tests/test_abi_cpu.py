@@ -24,6 +24,7 @@ def lib():
 def test_header_symbols_exported(lib):
     hdr = open(os.path.join(ROOT, "include", "dmrg.h")).read()
     declared = set(re.findall(r"^(?:int|int64_t|const char\*)\s+(dmrg_\w+)\(", hdr, re.M))
+    assert "dmrg_batch_sweep" in declared
     assert declared == set(lib.EXPORTED)
     so = lib.load_library()
     for name in declared:
