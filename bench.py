@@ -11,9 +11,12 @@ truncation, renormalization of every normal and complementary operator) in the m
 path (FP32 operator contractions, FP64 Davidson / eigensolver / energy).
 
 Reported: value = H_eff psi TFLOP/s over the timed steps (algorithmic flops of every
-H_eff product / wall time of the steps), the H_eff products' own device time and their
-HBM roofline, seconds per sweep at M = 4096, the FP64 path on the same step and the
-energy difference between the two, and the FP64 CPU oracle as the CPU baseline.
+H_eff product / device time of the whole steps, CUDA events), the H_eff products' own
+device time and their HBM roofline, the FP64 path on the same superblock and the energy
+difference between the two, e2e = the same metric over a whole job through the public API
+(fresh context from host arrays, block build, one sweep at M = 4096 from the starting
+state, energy read back; wall clock), sweep_s = that sweep's seconds, a batch of 32
+small instances looped vs batched, and the FP64 CPU oracle as the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -213,7 +216,62 @@ def _cpu_baseline_subprocess(steps, warmup):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
+def batch_instances(M_cap):
+    """Batch workload: 32 instances, even i -> sd, odd i -> pf; N_p = 2 + (7 i mod 9),
+    N_n = 2 + (5 i mod 9) capped at the space; M = 128 * 2^(i mod 5) capped; seeds 1000+i."""
+    from gen import make_problem, SPACES
+    out = []
+    for i in range(32):
+        space = "sd" if i % 2 == 0 else "pf"
+        cap = SPACES[space].states_per_species - 2
+        Np = min(2 + (7 * i) % 9, cap)
+        Nn = min(2 + (5 * i) % 9, cap)
+        M = min(128 * 2 ** (i % 5), M_cap)
+        out.append((make_problem(space, Np, Nn, (Np + Nn) % 2, seed=1000 + i), M, 2000 + i))
+    return out
+
+
+def run_batch_compare(P, M_cap):
+    """One sweep of every instance: looped one context at a time, then as one batch."""
+    import torch
+    from gen import initial_mps
+    inst = batch_instances(M_cap)
+    inits = [initial_mps(prob, M, s) for prob, M, s in inst]
+
+    def make():
+        ds = []
+        for (prob, M, s), init in zip(inst, inits):
+            d = P.DMRG(prob, precision=P.MIXED_FP32)
+            d.build_blocks(init)
+            ds.append(d)
+        return ds
+    loop = make()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_loop = [d.sweep(M)[1] for d, (_, M, _) in zip(loop, inst)]
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    c_loop = sum(d.counters()["launches"] for d in loop[:1])
+    bat = make()
+    b = P.Batch(bat)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_bat, st = b.sweep([M for _, M, _ in inst])
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    dE = max(abs(a - c) for a, c in zip(e_loop, e_bat))
+    b.close()
+    return {"instances": len(inst), "M_cap": M_cap, "loop_sweep_s": t_loop,
+            "batch_sweep_s": t_bat, "speedup": t_loop / t_bat,
+            "batched_products": st["products"], "batched_heff_device_s": st["heff_seconds"],
+            "max_dE_batch_vs_loop": dE,
+            "workload": "32 instances: even i sd, odd i pf, N_p=2+(7i mod 9), N_n=2+(5i mod 9), "
+                        "M=128*2^(i mod 5) capped at %d, seeds 1000+i, mixed path" % M_cap}
+
+
 def run_gpu(args):
+    import ctypes
+    import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -277,30 +335,8 @@ def run_gpu(args):
     value = world * flops / total_s / 1e12
     peak, peak_kind = _peaks()
     achieved = heff_bytes / max(heff_s, 1e-12) / 1e9
-    # end to end through the public API with host buffers: H_eff products at the next
-    # position, psi copied host->device and the result device->host every product
     p_e2e, _ = seq[-1]
     lay = d.psi_layout(p_e2e)
-    f_e2e, b_e2e, _ = d.heff_cost(p_e2e)
-    xh = torch.randn(lay["size"], dtype=torch.float64).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty(lay["size"], dtype=torch.float64, device="cuda")
-    yd = torch.empty_like(xd)
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        d.heff_apply(p_e2e, xd, yd)
-        yh.copy_(yd, non_blocking=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(args.steps, 3)
-    e0.record()
-    for _ in range(reps):
-        xd.copy_(xh, non_blocking=True)
-        d.heff_apply(p_e2e, xd, yd)
-        yh.copy_(yd, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3 / reps
     # FP64 path on the same superblock: Davidson from the mixed eigenvector
     psi_m = torch.empty(lay["size"], dtype=torch.float64, device="cuda")
     e_mixed, st_m = d.davidson(p_e2e, out=psi_m, allow_noconv=True)
@@ -311,15 +347,40 @@ def run_gpu(args):
     fp64_tf = (c3["heff_flops"] - c2["heff_flops"]) / max(c3["heff_seconds"] - c2["heff_seconds"],
                                                            1e-12) / 1e12
     d.set_options(precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
-    # one full sweep at M = 4096 in the mixed path
+    d.close()
+    del d
+    # end to end through the public API: a fresh context from the host arrays of the
+    # Hamiltonian and the starting state (copied to the device inside the timed region),
+    # the block build, one full sweep at M, the energy read back to the host
+    e2e = None
     sweep_s = None
     if args.sweep:
+        h2d = sum(int(a.nbytes) for a in (prob.species, prob.two_m, prob.eps, prob.v_idx,
+                                          prob.v_val, prob.order))
+        h2d += sum(int(np.asarray(a).nbytes) for a in init.flat())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sw_steps, _ = d.sweep(M)
+        dj = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
+        dj.build_blocks(init)
+        t1 = time.perf_counter()
+        sw_steps, e_sweep = dj.sweep(M)
         torch.cuda.synchronize()
-        sweep_s = time.perf_counter() - t0
+        t2 = time.perf_counter()
+        sweep_s = t2 - t1
+        sw_flops = sum(s["heff_flops"] * s["n_products"] for s in sw_steps)
+        e2e = {"value": sw_flops / (t2 - t0) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8 + len(sw_steps) * ctypes.sizeof(P.StepStats),
+               "job": "create from host arrays + block build + one sweep (%d steps, %d H_eff "
+                      "products) + energy read back; wall clock" % (len(sw_steps),
+                      sum(s["n_products"] for s in sw_steps)),
+               "build_s": t1 - t0, "sweep_energy": e_sweep}
+        dj.close()
+        del dj
     clocks = clk.summary()
+    batch = None
+    if args.batch_mcap > 0:
+        batch = run_batch_compare(P, args.batch_mcap)
     if rank != 0:
         return 0
     cpu = None
@@ -343,12 +404,11 @@ def run_gpu(args):
                  "energy_mixed": e_mixed, "dE_mixed_vs_fp64": abs(e_mixed - e_fp64)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "H_eff product (task-list GEMM stages)",
+                     "kernel": "H_eff product: k_pad_psi + k_heff_tc + k_heff_reduce + k_out_to_f64, CUDA events on the context stream around each product",
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
-        "e2e": {"value": f_e2e / e2e_s / 1e12, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": int(lay["size"]) * 8,
-                "d2h_bytes_per_step": int(lay["size"]) * 8},
+        "batch": batch,
+        "e2e": e2e,
         "gpu_launches": int(c1["launches"] - c0["launches"]),
         "phase_s": {k: c1[k] - c0[k] for k in ("t_enlarge", "t_super", "t_davidson",
                                                "t_truncate", "t_project", "t_predict")},
@@ -372,6 +432,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--sweep", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-mcap", type=int, default=256,
+                    help="M cap of the 32-instance batch-vs-loop comparison (0: skip)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")
