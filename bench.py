@@ -322,6 +322,8 @@ def run_gpu(args):
         if dist:
             dist.barrier()
     c1 = d.counters()
+    free_b, total_b = torch.cuda.mem_get_info()
+    dev_used_gb = (total_b - free_b) / 1e9
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(timed))]
     total_s = sum(step_ms) / 1e3
     if dist:
@@ -410,8 +412,15 @@ def run_gpu(args):
         "batch": batch,
         "e2e": e2e,
         "gpu_launches": int(c1["launches"] - c0["launches"]),
+        "device_mem_used_gb": dev_used_gb,
         "phase_s": {k: c1[k] - c0[k] for k in ("t_enlarge", "t_super", "t_davidson",
-                                               "t_truncate", "t_project", "t_predict")},
+                                               "t_truncate", "t_project", "t_predict",
+                                               "t_sync", "t_enlarge_host", "t_upload")},
+        "upload_bytes": c1["upload_bytes"] - c0["upload_bytes"],
+        "pool_mallocs": c1["pool_mallocs"] - c0["pool_mallocs"],
+        "host_detail_s": [b - a for a, b in zip(c0["t_detail"], c1["t_detail"])],
+        "superblock": {k: c1[k] for k in ("sb_blocks_l", "sb_blocks_r", "sb_terms", "sb_tiles",
+                                           "sb_small_tiles")},
         "clocks": clocks,
         "energies": [s["energy"] for s in stats],
         "step_ms": step_ms,

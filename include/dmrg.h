@@ -117,12 +117,29 @@ typedef struct {
   double heff_flops;
   double heff_bytes;
   double t_enlarge, t_super, t_davidson, t_truncate, t_project, t_predict;
+  double t_sync;            /* host seconds blocked waiting for the context stream      */
+  double t_enlarge_host;    /* host seconds of the enlargement's block discovery        */
+  double t_upload;          /* host seconds inside table uploads (all contexts)         */
+  int64_t upload_bytes;     /* bytes of those uploads (all contexts)                    */
+  int64_t sb_blocks_l, sb_blocks_r, sb_terms, sb_tiles;   /* last superblock built (tiles:
+                                                             32 x 32 tile kernels)       */
+  /* finer host seconds: [0] superblock term lists, [1] product tiles, [2] tile validation
+   * and uploads, [3] diagonal tasks, [4] renormalization tables, [5] renormalization
+   * GEMMs (waited for), [6] operator index tables, [7] enlargement kernels (waited for),
+   * [8] enlarged layouts, [9] source index uploads, [10] enlargement bitsets,
+   * [11] enlargement block discovery, [12] enlarged block tables, [13] enlarged arena
+   * allocation, [14] enlargement table uploads, [15] cudaMalloc calls (all contexts) */
+  double t_detail[16];
+  int64_t pool_mallocs;     /* device allocations that missed the caching pool          */
+  int64_t sb_small_tiles;   /* last superblock: tiles of the small-block product kernel */
 } dmrg_counters;
 
 /* Create a context for one problem (Eq. 1 and a target state).  Validates the input
  * (permutation, index ranges, i<j and k<l, quantum-number conservation, Hermitian list)
  * and builds the normal / complementary operator partition on the host.  Status:
- * DMRG_EINVAL on invalid input, DMRG_ENOMEM. */
+ * DMRG_EINVAL on invalid input, DMRG_ENOMEM.  The first call in a process sets glibc's
+ * mmap threshold to 32 MB and its trim threshold to 1 GB (mallopt), so that the host
+ * tables rebuilt at every step reuse heap memory instead of being paged in again. */
 int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dmrg_ctx** out);
 
 /* Release every host and device resource of the context.  NULL is accepted. */

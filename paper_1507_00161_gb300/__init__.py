@@ -89,7 +89,12 @@ class Counters(ctypes.Structure):
                 ("heff_bytes", ctypes.c_double), ("t_enlarge", ctypes.c_double),
                 ("t_super", ctypes.c_double), ("t_davidson", ctypes.c_double),
                 ("t_truncate", ctypes.c_double), ("t_project", ctypes.c_double),
-                ("t_predict", ctypes.c_double)]
+                ("t_predict", ctypes.c_double), ("t_sync", ctypes.c_double),
+                ("t_enlarge_host", ctypes.c_double), ("t_upload", ctypes.c_double),
+                ("upload_bytes", ctypes.c_int64), ("sb_blocks_l", ctypes.c_int64),
+                ("sb_blocks_r", ctypes.c_int64), ("sb_terms", ctypes.c_int64),
+                ("sb_tiles", ctypes.c_int64), ("t_detail", ctypes.c_double * 16),
+                ("pool_mallocs", ctypes.c_int64), ("sb_small_tiles", ctypes.c_int64)]
 
 
 _lib = None
@@ -206,7 +211,8 @@ class DMRG:
     def counters(self):
         c = Counters()
         self._check(self.lib.dmrg_get_counters(self.h, ctypes.byref(c)))
-        return {f: getattr(c, f) for f, _ in Counters._fields_}
+        return {f: (list(getattr(c, f)) if f == "t_detail" else getattr(c, f))
+                for f, _ in Counters._fields_}
 
     def close(self):
         if getattr(self, "h", None):

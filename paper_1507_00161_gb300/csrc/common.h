@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <array>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,10 @@
 namespace dmrg {
 
 extern std::atomic<int64_t> g_launches;
+// host -> device uploads of bookkeeping tables (bytes, host nanoseconds blocked in the copy)
+extern std::atomic<int64_t> g_upload_bytes, g_upload_ns;
+// device allocations that missed the caching pool (count, host nanoseconds in cudaMalloc)
+extern std::atomic<int64_t> g_malloc_count, g_malloc_ns;
 
 // ---------------------------------------------------------------------------------------
 // errors: every failure inside the library throws Error; the C-ABI turns it into a status
@@ -110,7 +115,12 @@ struct Pool {
         return p;
       }
     void* p = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaMalloc(&p, c);
+    g_malloc_ns.fetch_add(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                              std::chrono::steady_clock::now() - t0).count(),
+                          std::memory_order_relaxed);
+    g_malloc_count.fetch_add(1, std::memory_order_relaxed);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       trim();
@@ -191,7 +201,14 @@ struct DevBuf {
   }
   void upload(const T* h, int64_t count, cudaStream_t s) {
     alloc(count);
-    if (count) DMRG_CUDA(cudaMemcpyAsync(p, h, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+    if (count) {
+      const auto t0 = std::chrono::steady_clock::now();
+      DMRG_CUDA(cudaMemcpyAsync(p, h, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+      g_upload_ns.fetch_add(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t0).count(),
+                            std::memory_order_relaxed);
+      g_upload_bytes.fetch_add(int64_t(sizeof(T)) * count, std::memory_order_relaxed);
+    }
   }
   void upload(const std::vector<T>& h, cudaStream_t s) { upload(h.data(), int64_t(h.size()), s); }
 };
@@ -388,6 +405,12 @@ struct HeffPtrs {
   T* P[kMaxInst];
   const int32_t* active;
 };
+// output blocks with m, n <= kSmallEdge whose terms all have dLi, dRi <= kSmallEdge go
+// to the warp-per-tile CUDA-core product (heff_small.cu); its tiles are whole blocks
+constexpr int kSmallEdge = 16;
+template <class T>
+void heff_small(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
+                const HeffPtrs<T>& ptrs, cudaStream_t s);
 template <class T>
 void heff_reduce(const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s);
 // mixed path: the same product with 3xTF32 warp MMAs (heff_tc.cu)
@@ -422,6 +445,22 @@ struct EnlBlock {
 struct LayDev {
   int32_t pblk0, pblk1, poff1, D;
 };
+// one operator block to renormalize: O (enlarged sectors so, si) at xoff -> O' at yoff,
+// intermediate O U_i at toff of the scratch
+struct ProjTask {
+  int64_t xoff, yoff, toff;
+  int32_t so, si;
+};
+// tile_beg1/2: [n + 1] prefix sums of the 32 x 32 tiles of stage 1 (D_o x m_i) and
+// stage 2 (m_o x m_i) per block
+void project_blocks(const ProjTask* tasks, const int64_t* tile_beg1, int64_t n_tiles1,
+                    const int64_t* tile_beg2, int64_t n_tiles2, int64_t n, const int32_t* D,
+                    const int32_t* m, const int64_t* uoff, const double* X, const double* U,
+                    double* T, double* Y, cudaStream_t s);
+// blocks with D_o, D_i <= 32 (one warp each, both products fused)
+void project_small(const ProjTask* tasks, int64_t n, const int32_t* D, const int32_t* m,
+                   const int64_t* uoff, const double* X, const double* U, double* Y,
+                   cudaStream_t s);
 void enlarge_blocks(const EnlBlock* blocks, int64_t n, const int32_t* eptr, const EntryDev* ents,
                     const int32_t* src_by_in, int src_nsec, const int64_t* src_boff,
                     const int32_t* src_dim, const int32_t* src_npart, const int8_t* src_lpar,

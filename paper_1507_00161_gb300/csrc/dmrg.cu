@@ -1,15 +1,18 @@
 // libdmrg: two-site DMRG on the GPU for the shell-model Hamiltonian of Eq. (1).
 //
-// Host code here does the integer bookkeeping (sectors, block lists, task lists); every
-// floating-point step runs in the kernels of kernels.cu:
-//   enlargement of block operators by one site (copy tasks), H_eff psi (two task-list
-//   GEMM stages per product), Davidson vector algebra and the Ritz problem, reduced
-//   density matrices, their eigendecomposition, selection of the kept states,
-//   renormalization of every normal and complementary operator, and the prediction of
-//   the next wave function.
+// Host code here does the integer bookkeeping (sectors, block lists, term and tile
+// tables); every floating-point step runs in kernels:
+//   enlargement of block operators by one site (k_enlarge, kernels.cu), H_eff psi (fused
+//   tile kernels: heff.cu FP64, heff_tc.cu split-TF32 tensor cores), Davidson vector
+//   algebra and the Ritz problem, reduced density matrices, their eigendecomposition and
+//   the selection of the kept states (kernels.cu), renormalization of every normal and
+//   complementary operator (renorm.cu), and the prediction of the next wave function.
+#include <malloc.h>
+
 #include <chrono>
 #include <cmath>
 #include <memory>
+#include <mutex>
 #include <set>
 #include <thread>
 
@@ -123,13 +126,13 @@ struct Super {
   };
   std::vector<Term> terms_host;
   DevBuf<HeffItem> fitems;
-  DevBuf<HeffTile> ftiles;
+  DevBuf<HeffTile> ftiles, stiles;   // tile kernels (32 x 32 tiles); small-block kernel
   DevBuf<HeffRed> fred;
-  int64_t n_ftiles = 0, n_fred = 0, p_elems = 0;
+  int64_t n_ftiles = 0, n_stiles = 0, n_fred = 0, p_elems = 0;
   std::vector<HeffItem> h_items;
-  std::vector<HeffTile> h_tiles;
+  std::vector<HeffTile> h_tiles, h_stiles;
   std::vector<HeffRed> h_red;
-  std::vector<double> h_cost;
+  std::vector<double> h_cost, h_scost;
   // 16-byte aligned copy of psi used by the fused product
   std::vector<int64_t> pad_off;
   int64_t pad_size = 0;
@@ -153,6 +156,9 @@ struct dmrg_ctx {
   // wall seconds spent in the phases of a step (host bookkeeping + device work)
   double t_enlarge = 0, t_super = 0, t_davidson = 0, t_truncate = 0, t_project = 0,
          t_predict = 0;
+  double t_sync = 0, t_enlarge_host = 0;   // host blocked on the stream; enlarge host walk
+  int64_t last_sizes[5] = {0, 0, 0, 0, 0};   // last superblock: L, R blocks, terms, tiles, small tiles
+  double t_detail[16] = {};   // finer host phases (see dmrg.h)
   dmrg::Chain chain;
   dmrg::MPO mpo;
   dmrg_options opt{};
@@ -214,6 +220,13 @@ struct PhaseTimer {
   explicit PhaseTimer(double& a) : acc(a), t0(wall()) {}
   ~PhaseTimer() { acc += wall() - t0; }
 };
+
+// host waits for the context stream (time accumulated in t_sync)
+static void sync(Ctx& c) {
+  const double t0 = wall();
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  c.t_sync += wall() - t0;
+}
 
 static bool reachable(const std::set<std::tuple<int, int, int>>& s, const QN& q) {
   return s.count(std::make_tuple(q.a, q.b, q.m)) > 0;
@@ -323,14 +336,15 @@ static void ensure_dev_index(Ctx& c, OpSet& o) {
   o.dev_index_ready = true;
 }
 
+// fn(begin, end, thread) over [0, n) on up to 16 threads, at least `grain` items each
 template <class F>
-static void parallel_for(int n, F&& fn) {
+static void parallel_for(int n, F&& fn, int grain = 16) {
   int nt = int(std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency())));
-  if (n < 64 || nt <= 1) {
+  nt = std::min(nt, n / std::max(1, grain));
+  if (nt <= 1) {
     fn(0, n, 0);
     return;
   }
-  nt = std::min(nt, n / 16);
   std::vector<std::thread> th;
   for (int t = 0; t < nt; ++t) {
     const int a = int(int64_t(n) * t / nt), b = int(int64_t(n) * (t + 1) / nt);
@@ -341,75 +355,162 @@ static void parallel_for(int n, F&& fn) {
 
 static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& out) {
   PhaseTimer tm(c.t_enlarge);
+  const double th0 = wall();
+  double te = th0;
+  auto elap = [&](int i) {
+    const double t = wall();
+    c.t_detail[i] += t - te;
+    te = t;
+  };
   make_layout(c, blk.sec, s, left, lay);
   ensure_site_entries(c, s, left);
+  elap(8);
   ensure_dev_index(c, blk);
+  elap(9);
   const SiteEntries& se = left ? c.ent_left[s] : c.ent_right[s];
   const int nE = lay.sec.size();
   const int nsrc = blk.sec.size();
   const int ndst = int(se.ptr.size()) - 1;
   const auto& dq = left ? c.mpo.dq[s + 1] : c.mpo.dq[s];
-  // destination blocks (label k, Q_in) that receive at least one contribution
+  // destination blocks (label k, Q_in) that receive at least one contribution, with
+  // bitsets over the enlarged sectors: src[a][sigma] = {Q_in : source label a has a block
+  // whose input sector is the piece sigma of Q_in}; ok[d][sigma] = {Q_in : Q_in + d is an
+  // enlarged sector whose piece sigma exists}.  Label k gets the union over its W entries
+  // of src[e.src][sigma_in] & ok[d_k][sigma_out].
+  const QN qs = c.chain.q[s];
   QIndex qi_index(lay.sec);
-  std::vector<std::vector<EnlBlock>> part(16);
-  std::vector<std::vector<int32_t>> part_lab(16);
-  parallel_for(ndst, [&](int k0, int k1, int t) {
-    auto& v = part[t];
-    for (int k = k0; k < k1; ++k) {
-      // for the right side the operator's quantum-number change is minus that of the label
-      const QN d = left ? dq[k] : QN{0, 0, 0} - dq[k];
-      for (int Qi = 0; Qi < nE; ++Qi) {
-        const int Qo = qi_index.find(lay.sec.q[Qi] + d);
-        if (Qo < 0) continue;
-        bool exists = false;
-        for (int x = se.ptr[k]; x < se.ptr[k + 1] && !exists; ++x) {
-          const EntryDev& e = se.e[x];
-          for (int y = 0; y < 2 && !exists; ++y) {
-            const int so = kOpEntries[e.op][y][0], si = kOpEntries[e.op][y][1];
-            if (so < 0) continue;
-            const int qo = lay.pblk[Qo][so], qi = lay.pblk[Qi][si];
-            if (qo < 0 || qi < 0) continue;
-            if (blk.by_in[size_t(e.src) * nsrc + qi] >= 0) exists = true;
-          }
-        }
-        if (exists) v.push_back(EnlBlock{0, k, Qo, Qi, 0});
+  const int W64 = (nE + 63) / 64;
+  const int nsl = blk.nlab;
+  // enlarged sector of piece sigma of every source block sector
+  std::vector<int32_t> piece_sec(2 * size_t(nsrc));
+  for (int i = 0; i < nsrc; ++i) {
+    piece_sec[2 * i] = qi_index.find(blk.sec.q[i]);
+    piece_sec[2 * i + 1] = qi_index.find(blk.sec.q[i] + qs);
+  }
+  std::vector<uint64_t> src_bits(size_t(nsl) * 2 * W64, 0);
+  parallel_for(nsl, [&](int a0, int a1, int) {
+    for (int a = a0; a < a1; ++a) {
+      uint64_t* bits = &src_bits[size_t(a) * 2 * W64];
+      for (int64_t b = blk.lab_ptr[a]; b < blk.lab_ptr[a + 1]; ++b) {
+        const int32_t* ps = &piece_sec[2 * size_t(blk.blocks[b].si)];
+        if (ps[0] >= 0) bits[ps[0] / 64] |= uint64_t(1) << (ps[0] % 64);
+        if (ps[1] >= 0) bits[W64 + ps[1] / 64] |= uint64_t(1) << (ps[1] % 64);
       }
     }
   });
+  std::vector<QN> dk(ndst);
+  for (int k = 0; k < ndst; ++k) dk[k] = left ? dq[k] : QN{0, 0, 0} - dq[k];
+  std::vector<QN> dlist(dk);
+  std::sort(dlist.begin(), dlist.end());
+  dlist.erase(std::unique(dlist.begin(), dlist.end()), dlist.end());
+  const int nd = int(dlist.size());
+  std::vector<int32_t> dk_idx(ndst);
+  for (int k = 0; k < ndst; ++k)
+    dk_idx[k] = int32_t(std::lower_bound(dlist.begin(), dlist.end(), dk[k]) - dlist.begin());
+  std::vector<uint64_t> ok_bits(size_t(nd) * 2 * W64, 0);
+  std::vector<int32_t> qo_of(size_t(nd) * nE);
+  parallel_for(nd, [&](int d0, int d1, int) {
+    for (int di = d0; di < d1; ++di)
+      for (int Qi = 0; Qi < nE; ++Qi) {
+        const int Qo = qi_index.find(lay.sec.q[Qi] + dlist[di]);
+        qo_of[size_t(di) * nE + Qi] = Qo;
+        if (Qo < 0) continue;
+        for (int sg = 0; sg < 2; ++sg)
+          if (lay.pblk[Qo][sg] >= 0) ok_bits[(size_t(di) * 2 + sg) * W64 + Qi / 64] |= uint64_t(1) << (Qi % 64);
+      }
+  }, 2);
+  elap(10);
+  std::vector<std::vector<EnlBlock>> part(16);
+  std::vector<int64_t> part_elems(16, 0);
+  parallel_for(ndst, [&](int k0, int k1, int t) {
+    auto& v = part[t];
+    int64_t el = 0;
+    std::vector<uint64_t> acc(W64);
+    for (int k = k0; k < k1; ++k) {
+      const size_t di = size_t(dk_idx[k]);
+      std::fill(acc.begin(), acc.end(), 0);
+      for (int x = se.ptr[k]; x < se.ptr[k + 1]; ++x) {
+        const EntryDev& e = se.e[x];
+        for (int y = 0; y < 2; ++y) {
+          const int so = kOpEntries[e.op][y][0], si = kOpEntries[e.op][y][1];
+          if (so < 0) continue;
+          const uint64_t* sb = &src_bits[(size_t(e.src) * 2 + si) * W64];
+          const uint64_t* ob = &ok_bits[(di * 2 + so) * W64];
+          for (int w = 0; w < W64; ++w) acc[w] |= sb[w] & ob[w];
+        }
+      }
+      const int32_t* qo = &qo_of[di * nE];
+      for (int w = 0; w < W64; ++w)
+        for (uint64_t m = acc[w]; m; m &= m - 1) {
+          const int Qi = w * 64 + __builtin_ctzll(m);
+          v.push_back(EnlBlock{0, k, qo[Qi], Qi, 0});
+          el += (int64_t(lay.sec.d[qo[Qi]]) * lay.sec.d[Qi] + 3) & ~int64_t(3);
+        }
+    }
+    part_elems[t] = el;
+  });
+  elap(11);
+  // block offsets: every block starts on a 16-byte boundary (4 elements; vector loads of
+  // the fused product), i.e. block b starts at the sum of the rounded-up sizes before it.
+  // Threads own increasing label ranges, so concatenating their lists keeps label order.
+  const int nparts = int(part.size());
+  std::vector<int64_t> pbase(nparts + 1, 0), pelem(nparts + 1, 0);
+  for (int t = 0; t < nparts; ++t) {
+    pbase[t + 1] = pbase[t] + int64_t(part[t].size());
+    pelem[t + 1] = pelem[t] + part_elems[t];
+  }
   out.sec = lay.sec;
   out.nlab = ndst;
   out.lab_ptr.assign(ndst + 1, 0);
-  out.blocks.clear();
-  std::vector<EnlBlock> eb;
-  for (auto& v : part)
-    for (auto& b : v) eb.push_back(b);   // label order: threads own increasing label ranges
-  int64_t off = 0;
-  for (auto& b : eb) {
-    // 16-byte aligned block offsets (vector loads of the fused product), padded arena
-    off = (off + 3) & ~int64_t(3);
-    b.off = off;
-    out.blocks.push_back(OpBlock{b.Qo, b.Qi, off});
-    out.lab_ptr[b.k + 1]++;
-    off += int64_t(lay.sec.d[b.Qo]) * lay.sec.d[b.Qi];
+  out.blocks.resize(pbase[nparts]);
+  {
+    auto fill = [&](int t) {
+      int64_t off = pelem[t], idx = pbase[t];
+      for (EnlBlock& b : part[t]) {
+        b.off = off;
+        out.blocks[idx++] = OpBlock{b.Qo, b.Qi, off};
+        out.lab_ptr[b.k + 1]++;   // labels of one list belong to this list only
+        off += (int64_t(lay.sec.d[b.Qo]) * lay.sec.d[b.Qi] + 3) & ~int64_t(3);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nparts; ++t)
+      if (part[t].size() > 4096) th.emplace_back(fill, t);
+      else fill(t);
+    fill(0);
+    for (auto& x : th) x.join();
   }
   for (int k = 0; k < ndst; ++k) out.lab_ptr[k + 1] += out.lab_ptr[k];
-  out.n_elems = off;
+  out.n_elems = pelem[nparts];
+  elap(12);
   out.data.alloc(out.n_elems + 4);
+  elap(13);
   // layout table for the device
   std::vector<LayDev> ld(nE);
   for (int i = 0; i < nE; ++i) ld[i] = LayDev{lay.pblk[i][0], lay.pblk[i][1], lay.poff[i][1], lay.sec.d[i]};
   DevBuf<LayDev> dlay;
   DevBuf<EnlBlock> deb;
   dlay.upload(ld, c.stream);
-  deb.upload(eb, c.stream);
+  deb.alloc(std::max<int64_t>(pbase[nparts], 1));
+  for (int t = 0; t < nparts; ++t)
+    if (!part[t].empty())
+      DMRG_CUDA(cudaMemcpyAsync(deb.p + pbase[t], part[t].data(), sizeof(EnlBlock) * part[t].size(),
+                                cudaMemcpyHostToDevice, c.stream));
+  const int64_t n_eb = pbase[nparts];
   const auto& spar = left ? c.mpo.parity[s] : c.mpo.parity[s + 1];
+  elap(14);
+  c.t_enlarge_host += wall() - th0;
   DevBuf<int8_t> dpar;
   dpar.upload(spar, c.stream);
-  enlarge_blocks(deb.p, int64_t(eb.size()), se.dptr.p, se.de.p, blk.d_by_in.p, nsrc, blk.d_boff.p,
+  enlarge_blocks(deb.p, n_eb, se.dptr.p, se.de.p, blk.d_by_in.p, nsrc, blk.d_boff.p,
                  blk.d_dim.p, blk.d_npart.p, dpar.p, dlay.p, left ? 1 : 0, blk.data.p,
                  out.data.p, c.stream);
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));   // the small tables above are released
+  double tp = wall();
+  sync(c);   // the small tables above are released
+  c.t_detail[7] += wall() - tp;
+  tp = wall();
   out.index_by_in();
+  c.t_detail[6] += wall() - tp;
 }
 
 // stored block = kept part of an enlarged operator set: O' = U_o^T O U_i per block
@@ -431,8 +532,12 @@ static void project(Ctx& c, OpSet& E, const Iso& iso, OpSet& out) {
   out.nlab = E.nlab;
   out.lab_ptr.assign(E.nlab + 1, 0);
   out.blocks.clear();
-  TaskList A, B;
-  int64_t toff = 0, noff = 0;
+  double tp = wall();
+  // one renormalization task per kept block, read by k_project straight from this table
+  std::vector<ProjTask> tasks, small;
+  small.reserve(E.blocks.size());
+  std::vector<int64_t> tb1(1, 0), tb2(1, 0);
+  int64_t noff = 0, toff = 0;
   for (int k = 0; k < E.nlab; ++k) {
     out.lab_ptr[k] = int64_t(out.blocks.size());
     for (int64_t x = E.lab_ptr[k]; x < E.lab_ptr[k + 1]; ++x) {
@@ -440,36 +545,52 @@ static void project(Ctx& c, OpSet& E, const Iso& iso, OpSet& out) {
       const int no = iso.kept_idx[b.so], ni = iso.kept_idx[b.si];
       if (no < 0 || ni < 0) continue;
       const int Do = E.sec.d[b.so], Di = E.sec.d[b.si], mo = iso.m[b.so], mi = iso.m[b.si];
-      A.begin_task(Operand{toff, B_T, mi}, Do, mi);
-      A.add_term(Operand{b.off, B_X, Di}, Operand{iso.uoff[b.si], B_U, mi}, Di, 0, 1.0);
-      B.begin_task(Operand{noff, B_Y, mi}, mo, mi);
-      B.add_term(Operand{iso.uoff[b.so], B_U, mo}, Operand{toff, B_T, mi}, Do, 1, 1.0);
+      DMRG_REQUIRE(b.off + int64_t(Do) * Di <= E.n_elems, DMRG_EINVAL,
+                   "internal: operator block out of range");
       out.blocks.push_back(OpBlock{no, ni, noff});
-      toff += int64_t(Do) * mi;
+      if (Do <= 32 && Di <= 32) {
+        small.push_back(ProjTask{b.off, noff, 0, b.so, b.si});
+      } else {
+        tasks.push_back(ProjTask{b.off, noff, toff, b.so, b.si});
+        const int64_t ct = (mi + 31) / 32;
+        tb1.push_back(tb1.back() + (Do + 31) / 32 * ct);
+        tb2.push_back(tb2.back() + (mo + 31) / 32 * ct);
+        toff += int64_t(Do) * mi;
+      }
       noff += int64_t(mo) * mi;
     }
   }
   out.lab_ptr[E.nlab] = int64_t(out.blocks.size());
   out.n_elems = noff;
+  std::vector<int64_t> uo(nE);
+  for (int i = 0; i < nE; ++i) {
+    uo[i] = iso.uoff[i];
+    DMRG_REQUIRE(iso.m[i] == 0 || uo[i] + int64_t(E.sec.d[i]) * iso.m[i] <= iso.data.n,
+                 DMRG_EINVAL, "internal: isometry out of range");
+  }
   out.data.alloc(std::max<int64_t>(noff, 1));
   c.tmp.alloc(std::max<int64_t>(toff, 1));
-  DevTaskList dA, dB;
-  int64_t be[NBASE] = {0};
-  be[B_X] = E.data.n;
-  be[B_T] = c.tmp.n;
-  be[B_U] = iso.data.n;
-  be[B_Y] = out.data.n;
-  dA.build(A, be, c.stream);
-  dB.build(B, be, c.stream);
-  Bases<double> bb{};
-  bb.p[B_X] = E.data.p;
-  bb.p[B_T] = c.tmp.p;
-  bb.p[B_U] = iso.data.p;
-  bb.p[B_Y] = out.data.p;
-  run_gemm_tasks<double>(dA, bb, 1, c.stream);
-  run_gemm_tasks<double>(dB, bb, 1, c.stream);
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  DevBuf<ProjTask> dt, dts;
+  DevBuf<int32_t> dD, dm;
+  DevBuf<int64_t> duo, dtb1, dtb2;
+  dt.upload(tasks, c.stream);
+  dts.upload(small, c.stream);
+  dtb1.upload(tb1, c.stream);
+  dtb2.upload(tb2, c.stream);
+  dD.upload(E.sec.d, c.stream);
+  dm.upload(iso.m, c.stream);
+  duo.upload(uo, c.stream);
+  c.t_detail[4] += wall() - tp;
+  tp = wall();
+  project_small(dts.p, int64_t(small.size()), dD.p, dm.p, duo.p, E.data.p, iso.data.p,
+                out.data.p, c.stream);
+  project_blocks(dt.p, dtb1.p, tb1.back(), dtb2.p, tb2.back(), int64_t(tasks.size()), dD.p,
+                 dm.p, duo.p, E.data.p, iso.data.p, c.tmp.p, out.data.p, c.stream);
+  sync(c);
+  c.t_detail[5] += wall() - tp;
+  tp = wall();
   out.index_by_in();
+  c.t_detail[6] += wall() - tp;
 }
 
 static void identity_iso(Ctx& c, const Layout& lay, Iso& iso) {
@@ -565,8 +686,17 @@ static void build_super(Ctx& c, int p) {
     sb->d_pad_off.upload(sb->pad_off, c.stream);
     sb->d_pad_len.upload(len, c.stream);
   }
-  // H_eff items: (label k, L block, R block)
+  double tp = wall();
+  auto lap = [&](int i) {
+    const double t = wall();
+    c.t_detail[i] += t - tp;
+    tp = t;
+  };
+  // H_eff terms (label k, L block, R block) per output block, in label order; built in
+  // parallel over output blocks (the L block of label k into output sector Q has input
+  // sector Q - dq_k)
   const auto& par = c.mpo.parity[p + 1];
+  const auto& dqL = c.mpo.dq[p + 1];
   const int nlab = sb->L.nlab;
   DMRG_REQUIRE(nlab == sb->R.nlab, DMRG_EINVAL, "internal: label count mismatch");
   struct Item {
@@ -574,43 +704,77 @@ static void build_super(Ctx& c, int p) {
     int bin, bout;
     double sign;
   };
-  std::vector<std::vector<Item>> by_out(sb->bL.size());
-  std::vector<char> lused(sb->L.blocks.size(), 0), rused(sb->R.blocks.size(), 0);
-  for (int k = 0; k < nlab; ++k) {
-    for (int64_t x = sb->L.lab_ptr[k]; x < sb->L.lab_ptr[k + 1]; ++x) {
-      const OpBlock& lb = sb->L.blocks[x];
-      const int bin = sb->psi_of_L[lb.si], bout = sb->psi_of_L[lb.so];
-      if (bin < 0 || bout < 0) continue;
-      const int rb = sb->R.by_in[size_t(k) * nR + sb->bR[bin]];
-      if (rb < 0) continue;
-      DMRG_REQUIRE(sb->R.blocks[rb].so == sb->bR[bout], DMRG_EINVAL,
-                   "internal: superblock term breaks the target sector");
-      double sign = (par[k] && (particles(sb->Ll.sec.q[lb.si]) & 1)) ? -1.0 : 1.0;
-      by_out[bout].push_back(Item{x, rb, bin, bout, sign});
-      lused[x] = 1;
-      rused[rb] = 1;
+  const int nb = int(sb->bL.size());
+  QIndex qL(sb->Ll.sec);
+  std::vector<std::vector<Item>> by_out(nb);
+  std::atomic<bool> broken{false};
+  parallel_for(nb, [&](int b0, int b1, int) {
+    for (int bo = b0; bo < b1; ++bo) {
+      const int so = sb->bL[bo];
+      auto& v = by_out[bo];
+      for (int k = 0; k < nlab; ++k) {
+        const int si = qL.find(sb->Ll.sec.q[so] - dqL[k]);
+        if (si < 0) continue;
+        const int bin = sb->psi_of_L[si];
+        if (bin < 0) continue;
+        const int lb = sb->L.by_in[size_t(k) * nL + si];
+        if (lb < 0) continue;
+        const int rb = sb->R.by_in[size_t(k) * nR + sb->bR[bin]];
+        if (rb < 0) continue;
+        if (sb->L.blocks[lb].so != so || sb->R.blocks[rb].so != sb->bR[bo]) broken = true;
+        const double sign = (par[k] && (particles(sb->Ll.sec.q[si]) & 1)) ? -1.0 : 1.0;
+        v.push_back(Item{lb, rb, bin, bo, sign});
+      }
     }
+  });
+  DMRG_REQUIRE(!broken, DMRG_EINVAL, "internal: superblock term breaks the target sector");
+  lap(0);
+  // fused product: items grouped by output block, output tiles of at most 32 x 32, groups
+  // of at most G terms per thread block (partial tiles summed in group order); counts per
+  // output block first, then every block fills its own ranges in parallel
+  // small output blocks (every dimension of the block and of its terms <= kSmallEdge) are
+  // single tiles of the warp kernel with groups of at most Gs terms
+  const int G = 64, Gs = 16;
+  std::vector<int64_t> i_beg(nb + 1, 0), t_beg(nb + 1, 0), s_beg(nb + 1, 0), r_beg(nb + 1, 0),
+      p_beg(nb + 1, 0);
+  std::vector<char> small_bo(nb, 0);
+  for (int bo = 0; bo < nb; ++bo) {
+    const int ni = int(by_out[bo].size());
+    bool sm = sb->bdl[bo] <= kSmallEdge && sb->bdr[bo] <= kSmallEdge;
+    for (int j = 0; j < ni && sm; ++j) {
+      const int bin = by_out[bo][j].bin;
+      sm = sb->bdl[bin] <= kSmallEdge && sb->bdr[bin] <= kSmallEdge;
+    }
+    small_bo[bo] = sm;
+    const int groups = sm ? std::max(1, (ni + Gs - 1) / Gs) : std::max(1, (ni + G - 1) / G);
+    const int64_t tiles = sm ? 1 : int64_t((sb->bdl[bo] + 31) / 32) * ((sb->bdr[bo] + 31) / 32);
+    i_beg[bo + 1] = i_beg[bo] + ni;
+    t_beg[bo + 1] = t_beg[bo] + (sm ? 0 : tiles * groups);
+    s_beg[bo + 1] = s_beg[bo] + (sm ? groups : 0);
+    r_beg[bo + 1] = r_beg[bo] + (groups > 1 ? tiles : 0);
+    p_beg[bo + 1] = p_beg[bo] + (groups > 1 ? int64_t(groups) * sb->bdl[bo] * sb->bdr[bo] : 0);
   }
-  int64_t toff = 0;
-  double flops = 0;
-  int64_t items = 0;
-  // fused product: items grouped by output block, output tiles of at most 32 x 32
-  std::vector<HeffItem> fi;
+  DMRG_REQUIRE(i_beg[nb] < (int64_t(1) << 31), DMRG_EINVAL, "superblock has too many terms");
   struct TileCost {
     HeffTile t;
     double cost;
   };
-  std::vector<TileCost> ft;
-  std::vector<HeffRed> fr;
-  int64_t pelems = 0;
-  for (size_t bo = 0; bo < by_out.size(); ++bo) {
-    {
+  std::vector<HeffItem> fi(i_beg[nb]);
+  std::vector<TileCost> ft(t_beg[nb]), fts(s_beg[nb]);
+  std::vector<HeffRed> fr(r_beg[nb]);
+  std::vector<double> bo_flops(nb, 0.0);
+  std::vector<int64_t> bo_toff(nb, 0);
+  sb->terms_host.resize(i_beg[nb]);
+  parallel_for(nb, [&](int b0, int b1, int) {
+    for (int bo = b0; bo < b1; ++bo) {
       const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
-      const int i0 = int(fi.size());
-      double work = 0;
-      for (const Item& it : by_out[bo]) {
+      const int i0 = int(i_beg[bo]), i1 = int(i_beg[bo + 1]);
+      double work = 0, fl = 0;
+      int64_t to = 0;
+      for (int j = i0; j < i1; ++j) {
+        const Item& it = by_out[bo][j - i0];
         const int dLi = sb->bdl[it.bin], dRi = sb->bdr[it.bin];
-        HeffItem h;
+        HeffItem& h = fi[j];
         h.loff = sb->L.blocks[it.lb].off;
         h.roff = sb->R.blocks[it.rb].off;
         h.xoff = sb->pad_off[it.bin];
@@ -618,21 +782,29 @@ static void build_super(Ctx& c, int p) {
         h.dRi = dRi;
         h.sign = float(it.sign);
         h.pad = 0;
-        fi.push_back(h);
         work += double(dLi) * dRi + double(dLi);
+        to += int64_t(dLi) * dRo;
+        const double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;
+        const double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;
+        fl += std::min(f1, f2);
+        sb->terms_host[j] = Super::Term{it.lb, it.rb, it.bin, it.bout, it.sign};
       }
-      const int i1 = int(fi.size());
-      const int G = 64;   // terms per thread block
-      const int groups = std::max(1, (i1 - i0 + G - 1) / G);
-      for (int r0 = 0; r0 < dLo; r0 += 32)
-        for (int c0 = 0; c0 < dRo; c0 += 32) {
+      bo_flops[bo] = fl;
+      bo_toff[bo] = to;
+      const bool sm = small_bo[bo];
+      const int GG = sm ? Gs : G, edge = sm ? kSmallEdge : 32;
+      const int groups = std::max(1, (i1 - i0 + GG - 1) / GG);
+      int64_t tpos = sm ? s_beg[bo] : t_beg[bo], rpos = r_beg[bo], pelems = p_beg[bo];
+      std::vector<TileCost>& dst = sm ? fts : ft;
+      for (int r0 = 0; r0 < dLo; r0 += edge)
+        for (int c0 = 0; c0 < dRo; c0 += edge) {
           HeffTile t;
           t.yoff = sb->boff[bo];
           t.ld = dRo;
           t.r0 = r0;
           t.c0 = c0;
-          t.m = std::min(32, dLo - r0);
-          t.n = std::min(32, dRo - c0);
+          t.m = std::min(edge, dLo - r0);
+          t.n = std::min(edge, dRo - c0);
           t.inst = 0;
           const int64_t mn = int64_t(t.m) * t.n;
           if (groups > 1) {
@@ -647,34 +819,38 @@ static void build_super(Ctx& c, int p) {
             rd.groups = groups;
             rd.inst = 0;
             rd.pad = 0;
-            fr.push_back(rd);
+            fr[rpos++] = rd;
           }
           for (int g = 0; g < groups; ++g) {
-            t.i0 = i0 + g * G;
-            t.i1 = std::min(i1, t.i0 + G);
+            t.i0 = i0 + g * GG;
+            t.i1 = std::min(i1, t.i0 + GG);
             t.poff = groups > 1 ? pelems + g * mn : -1;
-            ft.push_back(TileCost{t, work * double(t.i1 - t.i0) / std::max(1, i1 - i0) * t.n + 1.0});
+            dst[tpos++] = TileCost{t, work * double(t.i1 - t.i0) / std::max(1, i1 - i0) * t.n + 1.0};
           }
           if (groups > 1) pelems += groups * mn;
         }
     }
-    if (by_out[bo].empty()) continue;
-    const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
-    for (const Item& it : by_out[bo]) {
-      const int dLi = sb->bdl[it.bin], dRi = sb->bdr[it.bin];
-      const OpBlock& lb = sb->L.blocks[it.lb];
-      const OpBlock& rb = sb->R.blocks[it.rb];
-      (void)lb;
-      (void)rb;
-      toff += int64_t(dLi) * dRo;
-      double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;
-      double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;
-      flops += std::min(f1, f2);
-      ++items;
-    }
+  });
+  int64_t toff = 0;
+  double flops = 0;
+  for (int bo = 0; bo < nb; ++bo) {
+    flops += bo_flops[bo];
+    toff += bo_toff[bo];
+  }
+  const int64_t items = i_beg[nb];
+  const int64_t pelems = p_beg[nb];
+  std::vector<char> lused(sb->L.blocks.size(), 0), rused(sb->R.blocks.size(), 0);
+  for (const auto& t : sb->terms_host) {
+    lused[t.lb] = 1;
+    rused[t.rb] = 1;
   }
   sb->t_elems = toff;
   sb->n_items = items;
+  c.last_sizes[0] = int64_t(sb->L.blocks.size());
+  c.last_sizes[1] = int64_t(sb->R.blocks.size());
+  c.last_sizes[2] = items;
+  c.last_sizes[3] = int64_t(ft.size());
+  c.last_sizes[4] = int64_t(fts.size());
   sb->flops = flops;
   double bytes = 0;
   for (size_t x = 0; x < lused.size(); ++x)
@@ -683,46 +859,56 @@ static void build_super(Ctx& c, int p) {
     if (rused[x]) bytes += double(sb->Rl.sec.d[sb->R.blocks[x].so]) * sb->Rl.sec.d[sb->R.blocks[x].si];
   bytes += 2.0 * double(sb->size);
   sb->bytes = bytes * (c.opt.precision == DMRG_FP64 ? 8.0 : 4.0);
-  // terms grouped by output block, kept on the host for the two-stage lists that only
-  // dmrg_psi_layout / dmrg_heff_apply build (the allocation-free product needs them)
-  for (size_t bo = 0; bo < by_out.size(); ++bo)
-    for (const Item& it : by_out[bo])
-      sb->terms_host.push_back({it.lb, it.rb, it.bin, it.bout, it.sign});
+  lap(1);
   {
     // heaviest tiles first; validate every access range on the host
-    std::stable_sort(ft.begin(), ft.end(),
-                     [](const TileCost& a, const TileCost& b) { return a.cost > b.cost; });
-    std::vector<HeffTile> tl(ft.size());
-    for (size_t i = 0; i < ft.size(); ++i) {
-      const HeffTile& t = ft[i].t;
-      tl[i] = t;
-      DMRG_REQUIRE(t.yoff + int64_t(t.r0 + t.m - 1) * t.ld + t.c0 + t.n - 1 < sb->size,
-                   DMRG_EINVAL, "internal: fused tile out of range");
-      for (int j = t.i0; j < t.i1; ++j) {
-        const HeffItem& h = fi[j];
-        DMRG_REQUIRE(h.loff + int64_t(t.r0 + t.m) * h.dLi - 1 < sb->L.n_elems &&
-                         h.roff + int64_t(t.c0 + t.n) * h.dRi - 1 < sb->R.n_elems &&
-                         h.xoff + int64_t(h.dLi) * h.dRi - 1 < sb->pad_size - 4,
-                     DMRG_EINVAL, "internal: fused item out of range");
+    auto by_cost = [](const TileCost& a, const TileCost& b) { return a.cost > b.cost; };
+    std::stable_sort(ft.begin(), ft.end(), by_cost);
+    std::stable_sort(fts.begin(), fts.end(), by_cost);
+    auto check = [&](const std::vector<TileCost>& v, std::vector<HeffTile>& tl, int edge) {
+      tl.resize(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        const HeffTile& t = v[i].t;
+        tl[i] = t;
+        DMRG_REQUIRE(t.m >= 1 && t.n >= 1 && t.m <= edge && t.n <= edge &&
+                         t.yoff + int64_t(t.r0 + t.m - 1) * t.ld + t.c0 + t.n - 1 < sb->size,
+                     DMRG_EINVAL, "internal: fused tile out of range");
+        for (int j = t.i0; j < t.i1; ++j) {
+          const HeffItem& h = fi[j];
+          DMRG_REQUIRE(h.loff + int64_t(t.r0 + t.m) * h.dLi - 1 < sb->L.n_elems &&
+                           h.roff + int64_t(t.c0 + t.n) * h.dRi - 1 < sb->R.n_elems &&
+                           h.xoff + int64_t(h.dLi) * h.dRi - 1 < sb->pad_size - 4 &&
+                           (edge == 32 || (h.dLi <= kSmallEdge && h.dRi <= kSmallEdge)),
+                       DMRG_EINVAL, "internal: fused item out of range");
+        }
       }
-    }
+    };
+    std::vector<HeffTile> tl, tls;
+    check(ft, tl, 32);
+    check(fts, tls, kSmallEdge);
     for (const HeffRed& r : fr)
       DMRG_REQUIRE(r.poff + int64_t(r.groups) * r.m * r.n <= pelems &&
                        r.yoff + int64_t(r.r0 + r.m - 1) * r.ld + r.c0 + r.n - 1 < sb->size,
                    DMRG_EINVAL, "internal: partial tile out of range");
     sb->fitems.upload(fi, c.stream);
     sb->ftiles.upload(tl, c.stream);
+    sb->stiles.upload(tls, c.stream);
     sb->fred.upload(fr, c.stream);
     // host copies for batch mode (lists of several instances in one launch)
-    sb->h_items = fi;
-    sb->h_tiles = tl;
-    sb->h_red = fr;
+    sb->h_items = std::move(fi);
+    sb->h_tiles = std::move(tl);
+    sb->h_stiles = std::move(tls);
+    sb->h_red = std::move(fr);
     sb->h_cost.resize(ft.size());
     for (size_t i = 0; i < ft.size(); ++i) sb->h_cost[i] = ft[i].cost;
-    sb->n_ftiles = int64_t(tl.size());
-    sb->n_fred = int64_t(fr.size());
+    sb->h_scost.resize(fts.size());
+    for (size_t i = 0; i < fts.size(); ++i) sb->h_scost[i] = fts[i].cost;
+    sb->n_ftiles = int64_t(sb->h_tiles.size());
+    sb->n_stiles = int64_t(sb->h_stiles.size());
+    sb->n_fred = int64_t(sb->h_red.size());
     sb->p_elems = pelems;
   }
+  lap(2);
   // diagonal tasks: terms that keep the sector (Delta q = 0)
   std::vector<DiagTask> dt;
   std::vector<DiagTerm> dg;
@@ -749,13 +935,14 @@ static void build_super(Ctx& c, int p) {
   sb->dtasks.upload(dt, c.stream);
   sb->dterms.upload(dg, c.stream);
   sb->n_dtasks = int(dt.size());
+  lap(3);
   if (c.opt.precision != DMRG_FP64) {
     sb->L.data32.alloc(sb->L.n_elems + 4);
     sb->R.data32.alloc(sb->R.n_elems + 4);
     to_f32(sb->L.data.p, sb->L.data32.p, sb->L.n_elems, c.stream);
     to_f32(sb->R.data.p, sb->R.data32.p, sb->R.n_elems, c.stream);
   }
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sync(c);
   c.sb = std::move(sb);
 }
 
@@ -794,7 +981,7 @@ static void ensure_two_stage(Ctx& c, Super& sb) {
   be[B_ROPS] = sb.R.n_elems;
   sb.st1.build(s1, be, c.stream);
   sb.st2.build(s2, be, c.stream);
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sync(c);
   sb.two_stage_ready = true;
 }
 
@@ -812,6 +999,7 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y) {
     ptr.X[0] = c.xpad64.p;
     ptr.Y[0] = y;
     ptr.P[0] = c.part64.p;
+    heff_small<double>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, c.stream);
     heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr,
                        c.stream);
   } else {
@@ -825,6 +1013,7 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y) {
     ptr.X[0] = c.xpad32.p;
     ptr.Y[0] = c.f32b.p;
     ptr.P[0] = c.part32.p;
+    heff_small<float>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, c.stream);
     heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, c.stream);
     to_f64(c.f32b.p, y, sb.size, c.stream);
   }
@@ -834,7 +1023,7 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y) {
 static void heff_timed(Ctx& c, Super& sb, const double* x, double* y) {
   if (c.ev_used + 2 > int(c.ev.size())) {
     // resolve what is pending before reusing events
-    DMRG_CUDA(cudaStreamSynchronize(c.stream));
+    sync(c);
     for (int i = 0; i + 1 < c.ev_used; i += 2) {
       float ms = 0;
       DMRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
@@ -857,7 +1046,7 @@ static void heff_timed(Ctx& c, Super& sb, const double* x, double* y) {
 }
 
 static double resolve_heff_timing(Ctx& c) {
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sync(c);
   for (int i = 0; i + 1 < c.ev_used; i += 2) {
     float ms = 0;
     DMRG_CUDA(cudaEventElapsedTime(&ms, c.ev[i], c.ev[i + 1]));
@@ -998,7 +1187,7 @@ struct DavPtrs {
 
 static void dav_readback(Ctx& c, const double* d, int cnt, double* h) {
   DMRG_CUDA(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.stream));
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sync(c);
 }
 static void dav_d2d(Ctx& c, double* dst, const double* src, int64_t n) {
   DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
@@ -1229,7 +1418,7 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     std::vector<double> kwh(ns);
     DMRG_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s));
     DMRG_CUDA(cudaMemcpyAsync(kwh.data(), kw, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
-    DMRG_CUDA(cudaStreamSynchronize(s));
+    sync(c);
     iso.lay = lay;
     iso.m.assign(ns, 0);
     iso.uoff.assign(ns, 0);
@@ -1246,7 +1435,7 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     iso.data.alloc(std::max<int64_t>(uo, 1));
     duoff.upload(iso.uoff, s);
     gather_u(droff.p, ddim.p, dkept.p, duoff.p, ns, c.eVs.p, iso.data.p, s);
-    DMRG_CUDA(cudaStreamSynchronize(s));
+    sync(c);
     iso.identity = false;
   }
   finish_iso_index(iso);
@@ -1382,7 +1571,7 @@ static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
   dot(g, g, sb.size, sc, c.partials.p, s);
   double nrm2 = 0;
   DMRG_CUDA(cudaMemcpyAsync(&nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
-  DMRG_CUDA(cudaStreamSynchronize(s));
+  sync(c);
   if (!(nrm2 > 0.0)) {
     uniform_guess(c, sb, g);
     return;
@@ -1549,6 +1738,17 @@ static int guarded(dmrg_ctx* c, F&& f) {
   }
 }
 
+// Host tables of the bookkeeping (tens of MB per step at large M) are allocated and freed
+// every step; glibc would return such blocks to the kernel and page them in again.  Keep
+// blocks up to 32 MB in the heap and never trim it, once per process.
+static void tune_host_allocator() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    mallopt(M_MMAP_THRESHOLD, 32 << 20);
+    mallopt(M_TRIM_THRESHOLD, 1 << 30);
+  });
+}
+
 extern "C" int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dmrg_ctx** out) {
   if (!out) return DMRG_EINVAL;
   *out = nullptr;
@@ -1558,6 +1758,7 @@ extern "C" int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dm
   } catch (...) {
     return DMRG_ENOMEM;
   }
+  tune_host_allocator();
   int st = guarded(c, [&] {
     DMRG_REQUIRE(opt != nullptr, DMRG_EINVAL, "options are NULL");
     c->opt = *opt;
@@ -1639,7 +1840,7 @@ extern "C" int dmrg_heff_apply(dmrg_ctx* c, int32_t p, const double* x, double* 
     Super& sb = super_at(*c, p);
     ensure_two_stage(*c, sb);
     heff(*c, sb, x, y);
-    DMRG_CUDA(cudaStreamSynchronize(c->stream));
+    sync(*c);
   });
 }
 
@@ -1663,7 +1864,7 @@ extern "C" int dmrg_davidson(dmrg_ctx* c, int32_t p, const double* guess, double
     if (out) {
       DMRG_CUDA(cudaMemcpyAsync(out, c->psi.p, sizeof(double) * sb.size, cudaMemcpyDeviceToDevice,
                                 c->stream));
-      DMRG_CUDA(cudaStreamSynchronize(c->stream));
+      sync(*c);
     }
     if (energy) *energy = r.theta;
     if (st) {
@@ -1772,6 +1973,18 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->t_truncate = c->t_truncate;
     out->t_project = c->t_project;
     out->t_predict = c->t_predict;
+    out->t_sync = c->t_sync;
+    out->t_enlarge_host = c->t_enlarge_host;
+    out->t_upload = 1e-9 * double(g_upload_ns.load());
+    out->upload_bytes = g_upload_bytes.load();
+    out->sb_blocks_l = c->last_sizes[0];
+    out->sb_blocks_r = c->last_sizes[1];
+    out->sb_terms = c->last_sizes[2];
+    out->sb_tiles = c->last_sizes[3];
+    out->sb_small_tiles = c->last_sizes[4];
+    for (int i = 0; i < 16; ++i) out->t_detail[i] = c->t_detail[i];
+    out->t_detail[15] = 1e-9 * double(g_malloc_ns.load());
+    out->pool_mallocs = g_malloc_count.load();
   });
 }
 
@@ -1805,7 +2018,7 @@ static void mlp_init(Ctx& c, uint64_t seed) {
   c.mlp_v.alloc(np);
   DMRG_CUDA(cudaMemsetAsync(c.mlp_m.p, 0, sizeof(float) * np, c.stream));
   DMRG_CUDA(cudaMemsetAsync(c.mlp_v.p, 0, sizeof(float) * np, c.stream));
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sync(c);
   c.mlp_ready = true;
   c.mlp_trained = false;
   c.mlp_step = 0;
@@ -1854,7 +2067,7 @@ extern "C" int dmrg_mlp_train(dmrg_ctx* c, int32_t epochs, int32_t batch, double
       }
       last = nbat ? tot / nbat : 0.0;
     }
-    DMRG_CUDA(cudaStreamSynchronize(c->stream));
+    sync(*c);
     c->mlp_trained = true;
     if (loss_out) *loss_out = last;
     if (n_samples) *n_samples = ns;
@@ -1870,13 +2083,13 @@ extern "C" int dmrg_mlp_params(dmrg_ctx* c, int32_t dir, double* host, int64_t n
       DMRG_REQUIRE(c->mlp_ready, DMRG_EINVAL, "network not initialised");
       DMRG_CUDA(cudaMemcpyAsync(f.data(), c->mlp_p.p, sizeof(float) * np, cudaMemcpyDeviceToHost,
                                 c->stream));
-      DMRG_CUDA(cudaStreamSynchronize(c->stream));
+      sync(*c);
       for (int64_t i = 0; i < np; ++i) host[i] = f[i];
     } else {
       if (!c->mlp_ready) mlp_init(*c, 1);
       for (int64_t i = 0; i < np; ++i) f[i] = float(host[i]);
       c->mlp_p.upload(f, c->stream);
-      DMRG_CUDA(cudaStreamSynchronize(c->stream));
+      sync(*c);
       c->mlp_trained = true;
     }
   });
@@ -1896,7 +2109,7 @@ static double loss_grad_t(Ctx& c, const double* P, const double* X, const double
   mlp_forward<T>(dp.p, dx.p, B, a, c.stream);
   const double loss = mlp_backward<T>(dp.p, dx.p, dt.p, B, a, dg.p, c.stream);
   DMRG_CUDA(cudaMemcpyAsync(hg.data(), dg.p, sizeof(T) * np, cudaMemcpyDeviceToHost, c.stream));
-  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  sync(c);
   for (int64_t i = 0; i < np; ++i) grad[i] = double(hg[i]);
   return loss;
 }
@@ -1936,9 +2149,9 @@ struct dmrg_batch {
   std::vector<cudaEvent_t> ev_ctx;
   // combined lists of the current step
   dmrg::DevBuf<dmrg::HeffItem> items;
-  dmrg::DevBuf<dmrg::HeffTile> tiles;
+  dmrg::DevBuf<dmrg::HeffTile> tiles, stiles;
   dmrg::DevBuf<dmrg::HeffRed> red;
-  int64_t n_tiles = 0, n_red = 0;
+  int64_t n_tiles = 0, n_stiles = 0, n_red = 0;
   // per-iteration tables: input and output vector pointers, active flags
   struct Tab {
     const double* in[dmrg::kMaxInst];
@@ -1976,32 +2189,43 @@ struct PoolScope {
 // concatenate the fused lists of the instances' current superblocks (heaviest tiles first)
 static void batch_lists(dmrg_batch& B, const std::vector<int>& inst) {
   std::vector<HeffItem> fi;
-  std::vector<std::pair<double, HeffTile>> ft;
+  std::vector<std::pair<double, HeffTile>> ft, fts;
   std::vector<HeffRed> fr;
   for (int i : inst) {
     Super& sb = *B.ctx[i]->sb;
     const int base = int(fi.size());
     fi.insert(fi.end(), sb.h_items.begin(), sb.h_items.end());
-    for (size_t t = 0; t < sb.h_tiles.size(); ++t) {
-      HeffTile x = sb.h_tiles[t];
-      x.i0 += base;
-      x.i1 += base;
-      x.inst = i;
-      ft.push_back({sb.h_cost[t], x});
-    }
+    auto add = [&](const std::vector<HeffTile>& tiles, const std::vector<double>& cost,
+                   std::vector<std::pair<double, HeffTile>>& dst) {
+      for (size_t t = 0; t < tiles.size(); ++t) {
+        HeffTile x = tiles[t];
+        x.i0 += base;
+        x.i1 += base;
+        x.inst = i;
+        dst.push_back({cost[t], x});
+      }
+    };
+    add(sb.h_tiles, sb.h_cost, ft);
+    add(sb.h_stiles, sb.h_scost, fts);
     for (HeffRed r : sb.h_red) {
       r.inst = i;
       fr.push_back(r);
     }
   }
-  std::stable_sort(ft.begin(), ft.end(),
-                   [](const auto& a, const auto& b) { return a.first > b.first; });
-  std::vector<HeffTile> tl(ft.size());
-  for (size_t t = 0; t < ft.size(); ++t) tl[t] = ft[t].second;
+  auto sorted = [](std::vector<std::pair<double, HeffTile>>& v) {
+    std::stable_sort(v.begin(), v.end(),
+                     [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<HeffTile> tl(v.size());
+    for (size_t t = 0; t < v.size(); ++t) tl[t] = v[t].second;
+    return tl;
+  };
+  const std::vector<HeffTile> tl = sorted(ft), tls = sorted(fts);
   B.items.upload(fi, B.bs);
   B.tiles.upload(tl, B.bs);
+  B.stiles.upload(tls, B.bs);
   B.red.upload(fr, B.bs);
   B.n_tiles = int64_t(tl.size());
+  B.n_stiles = int64_t(tls.size());
   B.n_red = int64_t(fr.size());
   DMRG_CUDA(cudaStreamSynchronize(B.bs));
 }
@@ -2024,6 +2248,7 @@ static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
       ptr.Y[i] = c.ybat64.p;
       ptr.P[i] = c.part64.p;
     }
+    heff_small<double>(B.stiles.p, B.n_stiles, B.items.p, ptr, B.bs);
     heff_fused<double>(B.tiles.p, B.n_tiles, B.items.p, B.red.p, B.n_red, ptr, B.bs);
     for (int i : inst) {
       Ctx& c = *B.ctx[i];
@@ -2043,6 +2268,7 @@ static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
       ptr.Y[i] = c.f32b.p;
       ptr.P[i] = c.part32.p;
     }
+    heff_small<float>(B.stiles.p, B.n_stiles, B.items.p, ptr, B.bs);
     heff_tc(B.tiles.p, B.n_tiles, B.items.p, B.red.p, B.n_red, ptr, B.bs);
     for (int i : inst) {
       Ctx& c = *B.ctx[i];

@@ -264,17 +264,18 @@ template void heff_reduce<double>(const HeffRed*, int64_t, const HeffPtrs<double
 template <class T>
 void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
                 const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  const size_t smem = sizeof(T) * kW * (kRingBytes / sizeof(T) + kXS);
-  static bool attr_set = false;   // per process: the attribute belongs to the kernel
-  if (!attr_set) {
-    DMRG_CUDA(cudaFuncSetAttribute(k_heff_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(smem)));
-    attr_set = true;
+  if (n_tiles > 0) {
+    const size_t smem = sizeof(T) * kW * (kRingBytes / sizeof(T) + kXS);
+    static bool attr_set = false;   // per process: the attribute belongs to the kernel
+    if (!attr_set) {
+      DMRG_CUDA(cudaFuncSetAttribute(k_heff_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem)));
+      attr_set = true;
+    }
+    k_heff_fused<T><<<int(n_tiles), kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
+    DMRG_LAUNCHED();
   }
-  k_heff_fused<T><<<int(n_tiles), kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
-  DMRG_LAUNCHED();
-  heff_reduce<T>(d_red, n_red, ptrs, s);
+  heff_reduce<T>(d_red, n_red, ptrs, s);   // partial tiles of both product kernels
 }
 template void heff_fused<double>(const HeffTile*, int64_t, const HeffItem*, const HeffRed*,
                                  int64_t, const HeffPtrs<double>&, cudaStream_t);

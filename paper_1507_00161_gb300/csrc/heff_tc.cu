@@ -328,17 +328,18 @@ __global__ void __launch_bounds__(kW * 32, 3)
 
 void heff_tc(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
              const HeffRed* d_red, int64_t n_red, const HeffPtrs<float>& ptrs, cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  const size_t smem = sizeof(float) * tc::kW * (tc::kRing + tc::kXS);
-  static bool attr_set = false;
-  if (!attr_set) {
-    DMRG_CUDA(cudaFuncSetAttribute(tc::k_heff_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(smem)));
-    attr_set = true;
+  if (n_tiles > 0) {
+    const size_t smem = sizeof(float) * tc::kW * (tc::kRing + tc::kXS);
+    static bool attr_set = false;
+    if (!attr_set) {
+      DMRG_CUDA(cudaFuncSetAttribute(tc::k_heff_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem)));
+      attr_set = true;
+    }
+    tc::k_heff_tc<<<int(n_tiles), tc::kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
+    DMRG_LAUNCHED();
   }
-  tc::k_heff_tc<<<int(n_tiles), tc::kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
-  DMRG_LAUNCHED();
-  heff_reduce<float>(d_red, n_red, ptrs, s);
+  heff_reduce<float>(d_red, n_red, ptrs, s);   // partial tiles of both product kernels
 }
 
 }  // namespace dmrg

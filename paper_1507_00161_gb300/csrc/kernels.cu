@@ -19,6 +19,8 @@
 namespace dmrg {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_upload_bytes{0}, g_upload_ns{0};
+std::atomic<int64_t> g_malloc_count{0}, g_malloc_ns{0};
 
 constexpr int kWarp = 32;
 
