@@ -132,6 +132,8 @@ typedef struct {
   double t_detail[16];
   int64_t pool_mallocs;     /* device allocations that missed the caching pool          */
   int64_t sb_small_tiles;   /* last superblock: tiles of the small-block product kernel */
+  int64_t sb_term_hist[8];  /* last superblock: terms whose largest inner dimension is
+                               <= 8, <= 16, <= 32, > 32 ([0..3]) and their flops ([4..7]) */
 } dmrg_counters;
 
 /* Create a context for one problem (Eq. 1 and a target state).  Validates the input

@@ -94,7 +94,8 @@ class Counters(ctypes.Structure):
                 ("upload_bytes", ctypes.c_int64), ("sb_blocks_l", ctypes.c_int64),
                 ("sb_blocks_r", ctypes.c_int64), ("sb_terms", ctypes.c_int64),
                 ("sb_tiles", ctypes.c_int64), ("t_detail", ctypes.c_double * 16),
-                ("pool_mallocs", ctypes.c_int64), ("sb_small_tiles", ctypes.c_int64)]
+                ("pool_mallocs", ctypes.c_int64), ("sb_small_tiles", ctypes.c_int64),
+                ("sb_term_hist", ctypes.c_int64 * 8)]
 
 
 _lib = None
@@ -211,7 +212,7 @@ class DMRG:
     def counters(self):
         c = Counters()
         self._check(self.lib.dmrg_get_counters(self.h, ctypes.byref(c)))
-        return {f: (list(getattr(c, f)) if f == "t_detail" else getattr(c, f))
+        return {f: (list(getattr(c, f)) if f in ("t_detail", "sb_term_hist") else getattr(c, f))
                 for f, _ in Counters._fields_}
 
     def close(self):

@@ -11,6 +11,8 @@
 
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <set>
@@ -158,6 +160,7 @@ struct dmrg_ctx {
          t_predict = 0;
   double t_sync = 0, t_enlarge_host = 0;   // host blocked on the stream; enlarge host walk
   int64_t last_sizes[5] = {0, 0, 0, 0, 0};   // last superblock: L, R blocks, terms, tiles, small tiles
+  int64_t term_hist[8] = {};   // last superblock: terms by largest inner dim; flops share
   double t_detail[16] = {};   // finer host phases (see dmrg.h)
   dmrg::Chain chain;
   dmrg::MPO mpo;
@@ -336,21 +339,95 @@ static void ensure_dev_index(Ctx& c, OpSet& o) {
   o.dev_index_ready = true;
 }
 
-// fn(begin, end, thread) over [0, n) on up to 16 threads, at least `grain` items each
+// Persistent host worker threads (created once per process): the bookkeeping runs many
+// short parallel loops per step, and starting threads for each would cost more than the
+// loops.  run(nt, job) calls job(t) for t = 0..nt-1, t = 0 on the calling thread.
+class WorkerPool {
+ public:
+  static WorkerPool& get() {
+    static WorkerPool pool;
+    return pool;
+  }
+  int size() const { return int(workers_.size()) + 1; }
+  // job(t) for every t in [0, n_tasks), claimed by the workers and the calling thread
+  void run(int n_tasks, const std::function<void(int)>& job) {
+    if (n_tasks <= 0) return;
+    if (n_tasks == 1 || workers_.empty()) {
+      for (int t = 0; t < n_tasks; ++t) job(t);
+      return;
+    }
+    std::unique_lock<std::mutex> caller(run_mu_);   // one parallel loop at a time
+    std::unique_lock<std::mutex> g(mu_);
+    job_ = &job;
+    n_tasks_ = n_tasks;
+    next_ = 0;
+    pending_ = n_tasks;
+    ++generation_;
+    cv_.notify_all();
+    claim(g);
+    done_cv_.wait(g, [&] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  WorkerPool() {
+    const int hw = int(std::max(1u, std::thread::hardware_concurrency()));
+    const int nw = std::min(16, hw) - 1;
+    for (int i = 0; i < nw; ++i) workers_.emplace_back([this] { loop(); });
+  }
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& w : workers_) w.join();
+  }
+  // run tasks of the current loop until none is left (mu_ held on entry and exit)
+  void claim(std::unique_lock<std::mutex>& g) {
+    while (next_ < n_tasks_) {
+      const int t = next_++;
+      const std::function<void(int)>* job = job_;
+      g.unlock();
+      (*job)(t);
+      g.lock();
+      if (--pending_ == 0) done_cv_.notify_all();
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> g(mu_);
+    for (;;) {
+      cv_.wait(g, [&] { return stop_ || (generation_ != seen && next_ < n_tasks_); });
+      if (stop_) return;
+      seen = generation_;
+      claim(g);
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* job_ = nullptr;
+  int n_tasks_ = 0, next_ = 0, pending_ = 0;
+  uint64_t generation_ = 0;
+  bool stop_ = false;
+};
+
+// fn(begin, end, part) over [0, n) in up to 16 parts of at least `grain` items each; part
+// p covers the p-th range in increasing order
 template <class F>
 static void parallel_for(int n, F&& fn, int grain = 16) {
-  int nt = int(std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency())));
-  nt = std::min(nt, n / std::max(1, grain));
+  WorkerPool& pool = WorkerPool::get();
+  int nt = std::min(pool.size(), n / std::max(1, grain));
   if (nt <= 1) {
     fn(0, n, 0);
     return;
   }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) {
+  const std::function<void(int)> job = [&](int t) {
     const int a = int(int64_t(n) * t / nt), b = int(int64_t(n) * (t + 1) / nt);
-    th.emplace_back([&fn, a, b, t] { fn(a, b, t); });
-  }
-  for (auto& x : th) x.join();
+    fn(a, b, t);
+  };
+  pool.run(nt, job);
 }
 
 static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& out) {
@@ -473,12 +550,7 @@ static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& ou
         off += (int64_t(lay.sec.d[b.Qo]) * lay.sec.d[b.Qi] + 3) & ~int64_t(3);
       }
     };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nparts; ++t)
-      if (part[t].size() > 4096) th.emplace_back(fill, t);
-      else fill(t);
-    fill(0);
-    for (auto& x : th) x.join();
+    WorkerPool::get().run(nparts, [&](int t) { fill(t); });
   }
   for (int k = 0; k < ndst; ++k) out.lab_ptr[k + 1] += out.lab_ptr[k];
   out.n_elems = pelem[nparts];
@@ -762,14 +834,16 @@ static void build_super(Ctx& c, int p) {
   std::vector<HeffItem> fi(i_beg[nb]);
   std::vector<TileCost> ft(t_beg[nb]), fts(s_beg[nb]);
   std::vector<HeffRed> fr(r_beg[nb]);
-  std::vector<double> bo_flops(nb, 0.0);
+  std::vector<double> bo_flops(nb, 0.0), bo_bytes(nb, 0.0);
   std::vector<int64_t> bo_toff(nb, 0);
+  std::vector<std::array<double, 8>> bo_hist(nb);
   sb->terms_host.resize(i_beg[nb]);
   parallel_for(nb, [&](int b0, int b1, int) {
     for (int bo = b0; bo < b1; ++bo) {
       const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
       const int i0 = int(i_beg[bo]), i1 = int(i_beg[bo + 1]);
-      double work = 0, fl = 0;
+      double work = 0, fl = 0, by = 0;
+      std::array<double, 8> hist{};
       int64_t to = 0;
       for (int j = i0; j < i1; ++j) {
         const Item& it = by_out[bo][j - i0];
@@ -787,9 +861,17 @@ static void build_super(Ctx& c, int p) {
         const double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;
         const double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;
         fl += std::min(f1, f2);
+        // an L block (label, input sector) and an R block each belong to one term only
+        by += double(dLo) * dLi + double(dRo) * dRi;
+        const int dmax = std::max(dLi, dRi);
+        const int cls = dmax <= 8 ? 0 : dmax <= 16 ? 1 : dmax <= 32 ? 2 : 3;
+        hist[cls] += 1.0;
+        hist[4 + cls] += std::min(f1, f2);
         sb->terms_host[j] = Super::Term{it.lb, it.rb, it.bin, it.bout, it.sign};
       }
       bo_flops[bo] = fl;
+      bo_bytes[bo] = by;
+      bo_hist[bo] = hist;
       bo_toff[bo] = to;
       const bool sm = small_bo[bo];
       const int GG = sm ? Gs : G, edge = sm ? kSmallEdge : 32;
@@ -832,18 +914,17 @@ static void build_super(Ctx& c, int p) {
     }
   });
   int64_t toff = 0;
-  double flops = 0;
+  double flops = 0, bytes = 0;
+  std::array<double, 8> hist{};
   for (int bo = 0; bo < nb; ++bo) {
     flops += bo_flops[bo];
+    bytes += bo_bytes[bo];
     toff += bo_toff[bo];
+    for (int i = 0; i < 8; ++i) hist[i] += bo_hist[bo][i];
   }
+  for (int i = 0; i < 8; ++i) c.term_hist[i] = int64_t(hist[i]);
   const int64_t items = i_beg[nb];
   const int64_t pelems = p_beg[nb];
-  std::vector<char> lused(sb->L.blocks.size(), 0), rused(sb->R.blocks.size(), 0);
-  for (const auto& t : sb->terms_host) {
-    lused[t.lb] = 1;
-    rused[t.rb] = 1;
-  }
   sb->t_elems = toff;
   sb->n_items = items;
   c.last_sizes[0] = int64_t(sb->L.blocks.size());
@@ -852,11 +933,6 @@ static void build_super(Ctx& c, int p) {
   c.last_sizes[3] = int64_t(ft.size());
   c.last_sizes[4] = int64_t(fts.size());
   sb->flops = flops;
-  double bytes = 0;
-  for (size_t x = 0; x < lused.size(); ++x)
-    if (lused[x]) bytes += double(sb->Ll.sec.d[sb->L.blocks[x].so]) * sb->Ll.sec.d[sb->L.blocks[x].si];
-  for (size_t x = 0; x < rused.size(); ++x)
-    if (rused[x]) bytes += double(sb->Rl.sec.d[sb->R.blocks[x].so]) * sb->Rl.sec.d[sb->R.blocks[x].si];
   bytes += 2.0 * double(sb->size);
   sb->bytes = bytes * (c.opt.precision == DMRG_FP64 ? 8.0 : 4.0);
   lap(1);
@@ -1982,6 +2058,7 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->sb_terms = c->last_sizes[2];
     out->sb_tiles = c->last_sizes[3];
     out->sb_small_tiles = c->last_sizes[4];
+    for (int i = 0; i < 8; ++i) out->sb_term_hist[i] = c->term_hist[i];
     for (int i = 0; i < 16; ++i) out->t_detail[i] = c->t_detail[i];
     out->t_detail[15] = 1e-9 * double(g_malloc_ns.load());
     out->pool_mallocs = g_malloc_count.load();

@@ -23,7 +23,7 @@ namespace {
 constexpr int kSmWarps = 8;
 
 template <class T>
-__global__ void __launch_bounds__(kSmWarps * 32)
+__global__ void __launch_bounds__(kSmWarps * 32, 3)
 k_heff_small(const HeffTile* __restrict__ tiles, int64_t n_tiles,
              const HeffItem* __restrict__ items, const HeffPtrs<T> ptrs) {
   __shared__ T Xs[kSmWarps][kSmallEdge * kSmallEdge];
@@ -43,33 +43,43 @@ k_heff_small(const HeffTile* __restrict__ tiles, int64_t n_tiles,
     T acc[kSmallEdge / 2];
 #pragma unroll
     for (int q = 0; q < kSmallEdge / 2; ++q) acc[q] = T(0);
-    for (int it = t.i0; it < t.i1; ++it) {
-      const HeffItem h = items[it];
-      const int dLi = h.dLi, dRi = h.dRi;
-      const T* __restrict__ Lb = L + h.loff + int64_t(t.r0) * dLi;
-      const T* __restrict__ Rb = R + h.roff + int64_t(t.c0 + c) * dRi;
-      const T* __restrict__ Xb = X + h.xoff;
-      if (on) {
-        for (int a = g; a < dLi; a += G) {
-          T s = T(0);
-          for (int b = 0; b < dRi; ++b) s = fma(Xb[a * dRi + b], Rb[b], s);
-          Xw[a * n + c] = s;
-        }
-      }
-      __syncwarp();
-      if (on) {
-        const T sg = T(h.sign);
-#pragma unroll
-        for (int q = 0; q < kSmallEdge / 2; ++q) {
-          const int i = g + q * G;
-          if (i < m) {
+    for (int base = t.i0; base < t.i1; base += 32) {
+      // the lanes load the next 32 term descriptors at once; each term broadcasts its own
+      HeffItem mine{};
+      if (base + lane < t.i1) mine = items[base + lane];
+      const int cnt = min(32, t.i1 - base);
+      for (int j = 0; j < cnt; ++j) {
+        const int64_t loff = __shfl_sync(0xffffffffu, (long long)mine.loff, j);
+        const int64_t roff = __shfl_sync(0xffffffffu, (long long)mine.roff, j);
+        const int64_t xoff = __shfl_sync(0xffffffffu, (long long)mine.xoff, j);
+        const int dLi = __shfl_sync(0xffffffffu, mine.dLi, j);
+        const int dRi = __shfl_sync(0xffffffffu, mine.dRi, j);
+        const float sign = __shfl_sync(0xffffffffu, mine.sign, j);
+        const T* __restrict__ Lb = L + loff + int64_t(t.r0) * dLi;
+        const T* __restrict__ Rb = R + roff + int64_t(t.c0 + c) * dRi;
+        const T* __restrict__ Xb = X + xoff;
+        if (on) {
+          for (int a = g; a < dLi; a += G) {
             T s = T(0);
-            for (int a = 0; a < dLi; ++a) s = fma(Lb[i * dLi + a], Xw[a * n + c], s);
-            acc[q] = fma(sg, s, acc[q]);
+            for (int b = 0; b < dRi; ++b) s = fma(Xb[a * dRi + b], Rb[b], s);
+            Xw[a * n + c] = s;
           }
         }
+        __syncwarp();
+        if (on) {
+          const T sg = T(sign);
+#pragma unroll
+          for (int q = 0; q < kSmallEdge / 2; ++q) {
+            const int i = g + q * G;
+            if (i < m) {
+              T s = T(0);
+              for (int a = 0; a < dLi; ++a) s = fma(Lb[i * dLi + a], Xw[a * n + c], s);
+              acc[q] = fma(sg, s, acc[q]);
+            }
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     if (on) {
       if (t.poff < 0) {
