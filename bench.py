@@ -288,7 +288,14 @@ def run_gpu(args):
         dist.barrier()
     import paper_1507_00161_gb300 as P
     from gen import make_problem, initial_mps
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    wname = WORKLOAD_NAME
+    if args.workload:
+        # another system of the same family (profiling of smaller cases)
+        sp, npr, nne, sd = args.workload.split(":")
+        w.update(space=sp, Np=int(npr), Nn=int(nne), seed=int(sd), two_Mz=(int(npr) + int(nne)) % 2)
+        wname = "%s shell, %dp+%dn, seed %d, M=%d (profiling case)" % (sp, int(npr), int(nne),
+                                                                       int(sd), args.M)
     M = args.M
     prob = make_problem(w["space"], w["Np"], w["Nn"], w["two_Mz"], seed=w["seed"])
     init = initial_mps(prob, M, w["mps_seed"])
@@ -393,7 +400,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "M": M, "positions": timed,
+        "config": {"workload": wname, "M": M, "positions": timed,
                    "precision": "FP32 contractions, FP64 Davidson/eigensolver/energy",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: %.0f MB of operator blocks per H_eff product"
@@ -443,6 +450,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-mcap", type=int, default=256,
                     help="M cap of the 32-instance batch-vs-loop comparison (0: skip)")
+    ap.add_argument("--workload", default="",
+                    help="space:Np:Nn:seed of another system (profiling of smaller cases)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")

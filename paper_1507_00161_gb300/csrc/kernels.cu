@@ -247,7 +247,16 @@ template void run_copy_tasks<float>(const CopyTask*, int64_t, const CopyTerm*,
 __constant__ int8_t c_op_entries[4][2][2] = {
     {{0, 0}, {1, 1}}, {{1, 1}, {-1, -1}}, {{1, 0}, {-1, -1}}, {{0, 1}, {-1, -1}}};
 
-__global__ void __launch_bounds__(256) k_enlarge(const EnlBlock* __restrict__ blocks, int64_t n,
+// One warp per enlarged block.  The block is made of up to four pieces (site states
+// sigma_out, sigma_in), each the size of one source block; every contribution (W entry,
+// site-operator element) fills one piece.  The lanes test 32 W entries at a time (source
+// block lookup, Jordan-Wigner sign) and list the contributions per piece in shared memory,
+// in entry order; each piece is then written once, its elements summed over its list in
+// that order (the same sum, in the same order, as zero-filling and adding one by one).
+constexpr int kEnlWarps = 8;
+constexpr int kEnlCap = 64;   // contributions per piece and pass
+
+__global__ void __launch_bounds__(kEnlWarps * 32) k_enlarge(const EnlBlock* __restrict__ blocks, int64_t n,
                                                  const int32_t* __restrict__ eptr,
                                                  const EntryDev* __restrict__ ents,
                                                  const int32_t* __restrict__ by_in, int nsrc,
@@ -258,38 +267,85 @@ __global__ void __launch_bounds__(256) k_enlarge(const EnlBlock* __restrict__ bl
                                                  const LayDev* __restrict__ lay, int left,
                                                  const double* __restrict__ src,
                                                  double* __restrict__ out) {
-  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
+  __shared__ int64_t s_off[kEnlWarps][4][kEnlCap];
+  __shared__ double s_sc[kEnlWarps][4][kEnlCap];
+  const int warp = threadIdx.x >> 5;
+  const int64_t w = int64_t(blockIdx.x) * kEnlWarps + warp;
   const int lane = threadIdx.x & (kWarp - 1);
   if (w >= n) return;
   const EnlBlock b = blocks[w];
   const LayDev lo = lay[b.Qo], li = lay[b.Qi];
   double* dst = out + b.off;
   const int Di = li.D;
-  for (int idx = lane; idx < lo.D * Di; idx += kWarp) dst[idx] = 0.0;
-  __syncwarp();
-  for (int x = eptr[b.k]; x < eptr[b.k + 1]; ++x) {
-    const EntryDev e = ents[x];
-    for (int y = 0; y < 2; ++y) {
-      const int so = c_op_entries[e.op][y][0], si = c_op_entries[e.op][y][1];
-      if (so < 0) continue;
-      const int qo = so ? lo.pblk1 : lo.pblk0, qi = si ? li.pblk1 : li.pblk0;
-      if (qo < 0 || qi < 0) continue;
-      const int sb = by_in[int64_t(e.src) * nsrc + qi];
-      if (sb < 0) continue;
-      double sc = e.coef;
-      if (left) {
-        if (e.op >= 2 && (npart[qi] & 1)) sc = -sc;
-      } else {
-        if (si && lpar[e.src]) sc = -sc;
+  const unsigned below = (1u << lane) - 1u;
+  const int x_end = eptr[b.k + 1];
+  int x0 = eptr[b.k];
+  bool first = true;   // the first pass writes, later passes (long lists) add
+  while (first || x0 < x_end) {
+    int cnt[4] = {0, 0, 0, 0};
+    while (x0 < x_end) {
+      const int x = x0 + lane;
+      int pc[2] = {-1, -1}, sbv[2] = {-1, -1};
+      double scv[2] = {0.0, 0.0};
+      if (x < x_end) {
+        const EntryDev e = ents[x];
+        for (int y = 0; y < 2; ++y) {
+          const int so = c_op_entries[e.op][y][0], si = c_op_entries[e.op][y][1];
+          if (so < 0) continue;
+          const int qo = so ? lo.pblk1 : lo.pblk0, qi = si ? li.pblk1 : li.pblk0;
+          if (qo < 0 || qi < 0) continue;
+          const int sb = by_in[int64_t(e.src) * nsrc + qi];
+          if (sb < 0) continue;
+          double sc = e.coef;
+          if (left) {
+            if (e.op >= 2 && (npart[qi] & 1)) sc = -sc;
+          } else {
+            if (si && lpar[e.src]) sc = -sc;
+          }
+          pc[y] = 2 * so + si;
+          sbv[y] = sb;
+          scv[y] = sc;
+        }
       }
-      const int rows = dim[qo], cols = dim[qi];
+      unsigned mask[4];
+      bool fits = true;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        mask[p] = __ballot_sync(0xffffffffu, pc[0] == p || pc[1] == p);
+        fits = fits && cnt[p] + __popc(mask[p]) <= kEnlCap;
+      }
+      if (!fits) break;   // this chunk opens the next pass
+      for (int y = 0; y < 2; ++y) {
+        if (pc[y] < 0) continue;
+        const int p = pc[y];
+        const int slot = cnt[p] + __popc(mask[p] & below);
+        s_off[warp][p][slot] = boff[sbv[y]];
+        s_sc[warp][p][slot] = scv[y];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p) cnt[p] += __popc(mask[p]);
+      x0 += kWarp;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int so = p >> 1, si = p & 1;
+      const int rows = so ? lo.D - lo.poff1 : lo.poff1;
+      const int cols = si ? li.D - li.poff1 : li.poff1;
+      if (rows <= 0 || cols <= 0 || (!first && cnt[p] == 0)) continue;
       const int ro = so ? lo.poff1 : 0, ri = si ? li.poff1 : 0;
-      const double* S = src + boff[sb];
+      const int64_t* offs = s_off[warp][p];
+      const double* scs = s_sc[warp][p];
       for (int idx = lane; idx < rows * cols; idx += kWarp) {
         const int r = idx / cols, cc = idx - r * cols;
-        dst[(int64_t)(ro + r) * Di + ri + cc] += sc * S[idx];
+        double* d = dst + (int64_t)(ro + r) * Di + ri + cc;
+        double acc = first ? 0.0 : *d;
+        for (int j = 0; j < cnt[p]; ++j) acc += scs[j] * src[offs[j] + idx];
+        *d = acc;
       }
     }
+    __syncwarp();
+    first = false;
   }
 }
 
@@ -298,8 +354,7 @@ void enlarge_blocks(const EnlBlock* blocks, int64_t n, const int32_t* eptr, cons
                     const int32_t* src_dim, const int32_t* src_npart, const int8_t* src_lpar,
                     const LayDev* lay, int left, const double* src, double* out, cudaStream_t s) {
   if (n <= 0) return;
-  const int64_t threads = n * kWarp;
-  k_enlarge<<<int((threads + 255) / 256), 256, 0, s>>>(blocks, n, eptr, ents, src_by_in, src_nsec,
+  k_enlarge<<<int((n + kEnlWarps - 1) / kEnlWarps), kEnlWarps * 32, 0, s>>>(blocks, n, eptr, ents, src_by_in, src_nsec,
                                                        src_boff, src_dim, src_npart, src_lpar, lay,
                                                        left, src, out);
   DMRG_LAUNCHED();
