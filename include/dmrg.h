@@ -128,8 +128,11 @@ typedef struct {
    * GEMMs (waited for), [6] operator index tables, [7] enlargement kernels (waited for),
    * [8] enlarged layouts, [9] source index uploads, [10] enlargement bitsets,
    * [11] enlargement block discovery, [12] enlarged block tables, [13] enlarged arena
-   * allocation, [14] enlargement table uploads, [15] cudaMalloc calls (all contexts) */
-  double t_detail[16];
+   * allocation, [14] enlargement table uploads, [15] cudaMalloc calls (all contexts),
+   * [16] Davidson: issuing the products, [17] Davidson: host work after each product,
+   * [18] Davidson: waits after each product, [19] Davidson iterations (a count),
+   * [20..23] reserved */
+  double t_detail[24];
   int64_t pool_mallocs;     /* device allocations that missed the caching pool          */
   int64_t sb_small_tiles;   /* last superblock: tiles of the small-block product kernel */
   int64_t sb_term_hist[8];  /* last superblock: terms whose largest inner dimension is

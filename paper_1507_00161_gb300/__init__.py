@@ -93,7 +93,7 @@ class Counters(ctypes.Structure):
                 ("t_enlarge_host", ctypes.c_double), ("t_upload", ctypes.c_double),
                 ("upload_bytes", ctypes.c_int64), ("sb_blocks_l", ctypes.c_int64),
                 ("sb_blocks_r", ctypes.c_int64), ("sb_terms", ctypes.c_int64),
-                ("sb_tiles", ctypes.c_int64), ("t_detail", ctypes.c_double * 16),
+                ("sb_tiles", ctypes.c_int64), ("t_detail", ctypes.c_double * 24),
                 ("pool_mallocs", ctypes.c_int64), ("sb_small_tiles", ctypes.c_int64),
                 ("sb_term_hist", ctypes.c_int64 * 8)]
 

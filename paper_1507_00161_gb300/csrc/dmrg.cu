@@ -161,7 +161,7 @@ struct dmrg_ctx {
   double t_sync = 0, t_enlarge_host = 0;   // host blocked on the stream; enlarge host walk
   int64_t last_sizes[5] = {0, 0, 0, 0, 0};   // last superblock: L, R blocks, terms, tiles, small tiles
   int64_t term_hist[8] = {};   // last superblock: terms by largest inner dim; flops share
-  double t_detail[16] = {};   // finer host phases (see dmrg.h)
+  double t_detail[24] = {};   // finer host phases (see dmrg.h)
   dmrg::Chain chain;
   dmrg::MPO mpo;
   dmrg_options opt{};
@@ -1401,8 +1401,14 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
   DavRun R;
   dav_begin(c, sb, guess, out, R);
   while (!R.done) {
+    double t0 = wall();
     heff_timed(c, sb, R.px, R.py);
+    const double t1 = wall(), s0 = c.t_sync;
     dav_after_product(c, R);
+    c.t_detail[16] += t1 - t0;
+    c.t_detail[17] += wall() - t1 - (c.t_sync - s0);
+    c.t_detail[18] += c.t_sync - s0;
+    c.t_detail[19] += 1.0;
   }
   R.res.heff_seconds = resolve_heff_timing(c);
   return R.res;
@@ -2059,7 +2065,7 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->sb_tiles = c->last_sizes[3];
     out->sb_small_tiles = c->last_sizes[4];
     for (int i = 0; i < 8; ++i) out->sb_term_hist[i] = c->term_hist[i];
-    for (int i = 0; i < 16; ++i) out->t_detail[i] = c->t_detail[i];
+    for (int i = 0; i < 24; ++i) out->t_detail[i] = c->t_detail[i];
     out->t_detail[15] = 1e-9 * double(g_malloc_ns.load());
     out->pool_mallocs = g_malloc_count.load();
   });

@@ -79,6 +79,22 @@ def test_davidson_first_step(P, space, Np, Nn, seed, M0):
     assert abs(abs(x @ x_ref) - 1.0) < 1e-8
 
 
+@pytest.mark.parametrize("space,Np,Nn,seed,M0", CASES)
+def test_mixed_energy_is_fp64_accurate(P, space, Np, Nn, seed, M0):
+    # mixed path: FP32 products inside Davidson, energy = FP64 Rayleigh quotient of the
+    # converged vector; the bound is the FP64 tolerance, not the FP32 one
+    prob = make_problem(space, Np, Nn, 1 if (Np + Nn) % 2 else 0, seed=seed)
+    init = initial_mps(prob, M0, seed + 100)
+    o = _oracle(prob, init)
+    sb = o.superblock(1)
+    from oracle.dmrg import davidson
+    e_ref, _, _, _ = davidson(sb.apply, sb.diagonal(), np.ones(sb.layout.size))
+    d = P.DMRG(prob, precision=P.MIXED_FP32)
+    d.build_blocks(init)
+    e, _ = d.davidson(1)
+    assert abs(e - e_ref) < 1e-8, (e, e_ref)
+
+
 def _compare_sweeps(P, prob, init, M, nsweeps):
     o = _oracle(prob, init)
     d = P.DMRG(prob)
@@ -132,8 +148,8 @@ def test_full_m_reproduces_exact_diagonalization(P):
 def test_fused_product_matches_two_stage(P):
     """Superblocks with sectors wider than 32 (chunked path, ring wrap-around), found near
     both ends of the chain after a sweep: the fused H_eff kernel against the independent
-    two-stage task-list product (the allocation-free entry point) in FP64, and the FP32
-    fused product against both."""
+    two-stage task-list product (the allocation-free entry point) in FP64, the FP32
+    fused product against both, and the energy of the mixed path against FP64 Davidson."""
     prob = make_problem("pf", 4, 4, 0, seed=2)
     d = P.DMRG(prob)
     d.build_blocks(initial_mps(prob, 2048, 2002))
@@ -154,12 +170,16 @@ def test_fused_product_matches_two_stage(P):
             continue          # intermediate larger than the fixed scratch
         err = (torch.linalg.norm(y1 - y2) / torch.linalg.norm(y2)).item()
         assert err <= 1e-12, (p, err)
+        e64, _ = d.davidson(p, allow_noconv=True)
         d.set_options(precision=P.MIXED_FP32)
         y3 = torch.empty_like(x)
         d.heff_apply(p, x, y3)
+        # energy of the mixed path (FP64 Rayleigh quotient) on wide sectors
+        e32, _ = d.davidson(p, allow_noconv=True)
         d.set_options(precision=P.FP64)
         err32 = (torch.linalg.norm(y3 - y2) / torch.linalg.norm(y2)).item()
         assert err32 <= 1e-5, (p, err32)
+        assert abs(e32 - e64) < 1e-8, (p, e32, e64)
         max_dl = max(max_dl, int(lay["dl"].max()))
         max_dr = max(max_dr, int(lay["dr"].max()))
         checked += 1
