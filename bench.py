@@ -36,6 +36,10 @@ METRIC = "H_eff·ψ TFLOP/s + sweep s at M=4096, mixed vs FP64 GPU at |ΔE|≤1e
 WORKLOAD = dict(space="pf", Np=8, Nn=8, two_Mz=0, seed=3, mps_seed=3003, M=4096)
 WORKLOAD_NAME = ("pf-shell 40 sites, 8p+8n, M_z=0 (m-scheme dim 1,087,455,228), random "
                  "J-coupled TBME sigma=1 MeV seed 3, M=4096, mid-chain two-site steps")
+# DRAM bytes (read + write) per mixed H_eff product of the default workload, from the one-pass
+# ncu capture of the timed steps in profiles/step_kernels_pf8p8n_M4096.md (sum over the
+# product's kernels / products); to be re-taken whenever those kernels change
+HEFF_TRAFFIC_BYTES = 175.2e6
 CPU_SAMPLE = dict(space="sd", Np=2, Nn=2, two_Mz=0, seed=1, mps_seed=5, M=64)
 
 
@@ -50,7 +54,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while running."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -64,7 +68,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -412,8 +416,10 @@ def run_gpu(args):
         "fp64": {"heff_tflops": fp64_tf, "energy": e_fp64, "products": st_d["n_products"],
                  "energy_mixed": e_mixed, "dE_mixed_vs_fp64": abs(e_mixed - e_fp64)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "H_eff product: k_pad_psi + k_heff_tc + k_heff_reduce + k_out_to_f64, CUDA events on the context stream around each product",
+                     "frac": achieved / peak,
+                     "traffic": HEFF_TRAFFIC_BYTES if not args.workload and M == WORKLOAD["M"]
+                     else None,
+                     "kernel": "H_eff product: k_pad_psi + k_heff_small + k_heff_tc + k_heff_reduce + k_to_f64, CUDA events on the context stream around each product",
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "batch": batch,

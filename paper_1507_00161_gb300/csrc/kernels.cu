@@ -407,6 +407,7 @@ void multidot(const double* const* d_vecs, int k, const double* w, int64_t n, do
               double* d_partials, cudaStream_t s) {
   if (k <= 0) return;
   k_multidot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(d_vecs, k, w, n, d_partials);
+  DMRG_LAUNCHED();
   k_multidot_final<<<k, 256, 0, s>>>(d_partials, k, kDotBlocks, d_out);
   DMRG_LAUNCHED();
 }
@@ -443,6 +444,7 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
 void dot(const double* a, const double* b, int64_t n, double* d_out, double* d_partials,
          cudaStream_t s) {
   k_dot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, n, d_partials);
+  DMRG_LAUNCHED();
   k_multidot_final<<<1, 256, 0, s>>>(d_partials, 1, kDotBlocks, d_out);
   DMRG_LAUNCHED();
 }
