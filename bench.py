@@ -242,10 +242,12 @@ def run_batch_compare(P, M_cap):
     inst = batch_instances(M_cap)
     inits = [initial_mps(prob, M, s) for prob, M, s in inst]
 
+    streams = [torch.cuda.Stream() for _ in inst]   # one stream per instance
+
     def make():
         ds = []
-        for (prob, M, s), init in zip(inst, inits):
-            d = P.DMRG(prob, precision=P.MIXED_FP32)
+        for (prob, M, s), init, st in zip(inst, inits, streams):
+            d = P.DMRG(prob, precision=P.MIXED_FP32, stream=st)
             d.build_blocks(init)
             ds.append(d)
         return ds
@@ -255,7 +257,12 @@ def run_batch_compare(P, M_cap):
     e_loop = [d.sweep(M)[1] for d, (_, M, _) in zip(loop, inst)]
     torch.cuda.synchronize()
     t_loop = time.perf_counter() - t0
-    c_loop = sum(d.counters()["launches"] for d in loop[:1])
+    cs = [d.counters() for d in loop]
+    loop_phases = {k: sum(c[k] for c in cs) for k in ("t_super", "t_enlarge", "t_davidson",
+                                                      "t_truncate", "t_sync", "pool_mallocs")}
+    loop_phases["t_malloc"] = cs[-1]["t_detail"][15]
+    loop_phases["t_dav_host"] = sum(c["t_detail"][17] for c in cs)
+    loop_phases["steps"] = sum(2 * (prob.n_sites - 3) for prob, _, _ in inst)
     bat = make()
     b = P.Batch(bat)
     torch.cuda.synchronize()
@@ -268,7 +275,7 @@ def run_batch_compare(P, M_cap):
     return {"instances": len(inst), "M_cap": M_cap, "loop_sweep_s": t_loop,
             "batch_sweep_s": t_bat, "speedup": t_loop / t_bat,
             "batched_products": st["products"], "batched_heff_device_s": st["heff_seconds"],
-            "max_dE_batch_vs_loop": dE,
+            "max_dE_batch_vs_loop": dE, "loop_phase_s": loop_phases,
             "workload": "32 instances: even i sd, odd i pf, N_p=2+(7i mod 9), N_n=2+(5i mod 9), "
                         "M=128*2^(i mod 5) capped at %d, seeds 1000+i, mixed path" % M_cap}
 

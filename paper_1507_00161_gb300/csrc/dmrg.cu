@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <exception>
 #include <functional>
 #include <memory>
 #include <mutex>
@@ -203,8 +204,12 @@ struct dmrg_ctx {
   int64_t heff_products = 0;
   double heff_seconds = 0, heff_flops = 0, heff_bytes = 0;
   double step_heff_seconds = 0;
+  // pinned host words for the small per-iteration readbacks (a copy into pageable memory
+  // goes through a staging buffer of the driver)
+  double* h_words = nullptr;
   ~dmrg_ctx() {
     for (auto e : ev) cudaEventDestroy(e);
+    if (h_words) cudaFreeHost(h_words);
   }
 };
 
@@ -344,29 +349,42 @@ static void ensure_dev_index(Ctx& c, OpSet& o) {
 // loops.  run(nt, job) calls job(t) for t = 0..nt-1, t = 0 on the calling thread.
 class WorkerPool {
  public:
+  // the bookkeeping loops of one context
   static WorkerPool& get() {
     static WorkerPool pool;
     return pool;
   }
+  // the instances of a batch (each instance's own loops then use get())
+  static WorkerPool& instances() {
+    static WorkerPool pool;
+    return pool;
+  }
   int size() const { return int(workers_.size()) + 1; }
-  // job(t) for every t in [0, n_tasks), claimed by the workers and the calling thread
+  // job(t) for every t in [0, n_tasks), claimed by the workers and the calling thread.  A
+  // call made while the pool is running another loop runs serially on the calling thread.
+  // The first exception of a job is rethrown once every job has finished.
   void run(int n_tasks, const std::function<void(int)>& job) {
     if (n_tasks <= 0) return;
-    if (n_tasks == 1 || workers_.empty()) {
+    std::unique_lock<std::mutex> caller(run_mu_, std::try_to_lock);
+    if (n_tasks == 1 || workers_.empty() || !caller.owns_lock()) {
       for (int t = 0; t < n_tasks; ++t) job(t);
       return;
     }
-    std::unique_lock<std::mutex> caller(run_mu_);   // one parallel loop at a time
     std::unique_lock<std::mutex> g(mu_);
     job_ = &job;
     n_tasks_ = n_tasks;
     next_ = 0;
     pending_ = n_tasks;
+    error_ = nullptr;
     ++generation_;
     cv_.notify_all();
     claim(g);
     done_cv_.wait(g, [&] { return pending_ == 0; });
     job_ = nullptr;
+    std::exception_ptr e = error_;
+    error_ = nullptr;
+    g.unlock();
+    if (e) std::rethrow_exception(e);
   }
 
  private:
@@ -389,8 +407,14 @@ class WorkerPool {
       const int t = next_++;
       const std::function<void(int)>* job = job_;
       g.unlock();
-      (*job)(t);
+      std::exception_ptr e;
+      try {
+        (*job)(t);
+      } catch (...) {
+        e = std::current_exception();
+      }
       g.lock();
+      if (e && !error_) error_ = e;
       if (--pending_ == 0) done_cv_.notify_all();
     }
   }
@@ -410,6 +434,7 @@ class WorkerPool {
   const std::function<void(int)>* job_ = nullptr;
   int n_tasks_ = 0, next_ = 0, pending_ = 0;
   uint64_t generation_ = 0;
+  std::exception_ptr error_;
   bool stop_ = false;
 };
 
@@ -1262,8 +1287,11 @@ struct DavPtrs {
 };
 
 static void dav_readback(Ctx& c, const double* d, int cnt, double* h) {
-  DMRG_CUDA(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.stream));
+  if (!c.h_words) DMRG_CUDA(cudaMallocHost(&c.h_words, sizeof(double) * 64));
+  DMRG_REQUIRE(cnt <= 64, DMRG_EINVAL, "internal: readback too long");
+  DMRG_CUDA(cudaMemcpyAsync(c.h_words, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.stream));
   sync(c);
+  for (int i = 0; i < cnt; ++i) h[i] = c.h_words[i];
 }
 static void dav_d2d(Ctx& c, double* dst, const double* src, int64_t n) {
   DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
@@ -1652,8 +1680,7 @@ static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
   double* sc = c.small.p + 64 * 64 * 6;
   dot(g, g, sb.size, sc, c.partials.p, s);
   double nrm2 = 0;
-  DMRG_CUDA(cudaMemcpyAsync(&nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
-  sync(c);
+  dav_readback(c, sc, 1, &nrm2);
   if (!(nrm2 > 0.0)) {
     uniform_guess(c, sb, g);
     return;
@@ -2434,7 +2461,11 @@ static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
   std::vector<int> inst;
   std::vector<DavRun> runs(B.ctx.size());
   std::vector<double> t0(B.ctx.size());
-  for (const BWork& w : work) {
+  // every instance's own bookkeeping (superblock, prediction, truncation, the host part of
+  // its Davidson iterations) runs on its own host thread and its own stream
+  WorkerPool& ip = WorkerPool::instances();
+  ip.run(int(work.size()), [&](int j) {
+    const BWork& w = work[j];
     Ctx& c = *B.ctx[w.inst];
     PoolScope ps(&c.pool);
     t0[w.inst] = now_s();
@@ -2443,8 +2474,8 @@ static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
     predict(c, sb, w.p, w.dir, c.psi_guess.p);
     c.psi.alloc(std::max<int64_t>(sb.size, 1));
     dav_begin(c, sb, c.psi_guess.p, c.psi.p, runs[w.inst]);
-    inst.push_back(w.inst);
-  }
+  });
+  for (const BWork& w : work) inst.push_back(w.inst);
   batch_buffers(B, inst);
   batch_lists(B, inst);
   if (B.exec) {
@@ -2457,13 +2488,15 @@ static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
     for (int i : inst) any = any || !runs[i].done;
     if (!any) break;
     batch_product(B, inst, runs);
-    for (int i : inst) {
-      if (runs[i].done) continue;
+    ip.run(int(inst.size()), [&](int j) {
+      const int i = inst[j];
+      if (runs[i].done) return;
       PoolScope ps(&B.ctx[i]->pool);
       dav_after_product(*B.ctx[i], runs[i]);
-    }
+    });
   }
-  for (const BWork& w : work) {
+  ip.run(int(work.size()), [&](int j) {
+    const BWork& w = work[j];
     Ctx& c = *B.ctx[w.inst];
     PoolScope ps(&c.pool);
     c.psi_valid = true;
@@ -2482,7 +2515,7 @@ static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
     s.heff_seconds = 0;
     s.heff_flops = flops;
     s.heff_bytes = bytes;
-  }
+  });
 }
 
 }  // namespace dmrg
@@ -2523,7 +2556,7 @@ extern "C" int dmrg_batch_create(int32_t n, dmrg_ctx* const* ctxs, dmrg_batch** 
       b->ctx.push_back(ctxs[i]);
     }
     b->precision = ctxs[0]->opt.precision;
-    DMRG_CUDA(cudaStreamCreate(&b->bs));
+    DMRG_CUDA(cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking));
     DMRG_CUDA(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
     b->ev_ctx.resize(n);
     for (int i = 0; i < n; ++i) DMRG_CUDA(cudaEventCreateWithFlags(&b->ev_ctx[i], cudaEventDisableTiming));

@@ -15,6 +15,8 @@
 // tile are added in group order by k_heff_reduce: the result is deterministic.
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.h"
 
 namespace dmrg {
@@ -266,12 +268,11 @@ void heff_fused(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_item
                 const HeffRed* d_red, int64_t n_red, const HeffPtrs<T>& ptrs, cudaStream_t s) {
   if (n_tiles > 0) {
     const size_t smem = sizeof(T) * kW * (kRingBytes / sizeof(T) + kXS);
-    static bool attr_set = false;   // per process: the attribute belongs to the kernel
-    if (!attr_set) {
+    static std::once_flag attr_once;   // per process: the attribute belongs to the kernel
+    std::call_once(attr_once, [&] {
       DMRG_CUDA(cudaFuncSetAttribute(k_heff_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(smem)));
-      attr_set = true;
-    }
+    });
     k_heff_fused<T><<<int(n_tiles), kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
     DMRG_LAUNCHED();
   }

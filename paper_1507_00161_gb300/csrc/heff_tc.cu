@@ -15,6 +15,8 @@
 // synchronously.  Deterministic: fixed term order per warp, fixed warp and group order.
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.h"
 
 namespace dmrg {
@@ -330,12 +332,11 @@ void heff_tc(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
              const HeffRed* d_red, int64_t n_red, const HeffPtrs<float>& ptrs, cudaStream_t s) {
   if (n_tiles > 0) {
     const size_t smem = sizeof(float) * tc::kW * (tc::kRing + tc::kXS);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_once;   // per process: the attribute belongs to the kernel
+    std::call_once(attr_once, [&] {
       DMRG_CUDA(cudaFuncSetAttribute(tc::k_heff_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(smem)));
-      attr_set = true;
-    }
+    });
     tc::k_heff_tc<<<int(n_tiles), tc::kW * 32, smem, s>>>(d_tiles, d_items, ptrs);
     DMRG_LAUNCHED();
   }

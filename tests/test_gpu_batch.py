@@ -21,12 +21,15 @@ def P():
     return P
 
 
-def _contexts(P, precision):
+def _contexts(P, precision, own_streams=False):
     out = []
     for space, Np, Nn, seed, M in INSTANCES:
         tm = 0 if (Np + Nn) % 2 == 0 else 1
         prob = make_problem(space, Np, Nn, tm, seed=seed)
-        d = P.DMRG(prob, precision=precision)
+        # batch contexts on streams of their own: their host work runs concurrently
+        st = torch.cuda.Stream() if own_streams else None
+        d = P.DMRG(prob, precision=precision, stream=st)
+        d._stream_ref = st
         d.build_blocks(initial_mps(prob, M, seed + 7))
         out.append(d)
     return out
@@ -37,7 +40,7 @@ def test_batch_sweep_equals_single_sweeps(P, precision):
     Ms = [x[4] for x in INSTANCES]
     alone = _contexts(P, precision)
     e_alone = [[d.sweep(M)[1] for _ in range(2)] for d, M in zip(alone, Ms)]
-    ctxs = _contexts(P, precision)
+    ctxs = _contexts(P, precision, own_streams=True)
     b = P.Batch(ctxs)
     e1, st1 = b.sweep(Ms)
     e2, st2 = b.sweep(Ms)
