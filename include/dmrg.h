@@ -14,7 +14,9 @@
  *   dmrg_destroy().  Arguments documented as "device" are CUDA device pointers owned by
  *   the caller; they must hold the stated number of float64 elements.
  * - All work is issued on the stream given in dmrg_options.stream (NULL: the legacy
- *   default stream).  Calls that return numbers to the host synchronise that stream.
+ *   default stream, which serialises with all other work on the device).  Calls that
+ *   return numbers to the host synchronise that stream.  Contexts meant to run at the
+ *   same time (the members of a batch) need streams of their own.
  * - Sectors are q = (N_p, N_n, 2M_z) integer triples in lexicographic order.  Chain
  *   position c holds site order[c]; bond b lies between positions b and b+1.
  * - A two-site step at position p (1 <= p <= N-3) treats the superblock
@@ -270,8 +272,11 @@ int dmrg_heff_cost(dmrg_ctx* ctx, int32_t p, double* flops, double* bytes, int64
  * (position order as in dmrg_sweep; contexts with fewer steps drop out), and every
  * Davidson iteration computes the H_eff products of all contexts still iterating in ONE
  * fused kernel launch (tiles of all superblocks in one list), recorded once per step in a
- * CUDA graph on an internal stream and replayed with new vector pointers.  Results are
- * identical to sweeping the contexts one by one.  M: [n] kept states per context;
+ * CUDA graph on an internal stream and replayed with new vector pointers.  Each context's
+ * own work (superblock, prediction, the host side of its Davidson iterations, truncation)
+ * runs on a host thread of its own and on the context's stream, so contexts created with
+ * distinct streams overlap.  Results are identical to sweeping the contexts one by one.
+ * M: [n] kept states per context;
  * energies: optional [n] energy of each context's last step. */
 typedef struct dmrg_batch dmrg_batch;
 typedef struct {
