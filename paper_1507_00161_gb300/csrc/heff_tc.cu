@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kW * 32, 3)
       ++issued;
       float* const Pc = ring;                 // psi chunk (kc x rc)
       float* const Rc = ring + kT * kT;       // R chunk (n x rc)
-      float* const Lc = ring + 2 * kT * kT;   // L chunk (m x kc)
+      float* const Lc = ring;                 // L chunk (m x kc), once psi and R are used
       for (int k0 = 0; k0 < dLi; k0 += kT) {
         const int kc = min(kT, dLi - k0);
         const int MT1 = (kc + 15) >> 4;
