@@ -207,7 +207,19 @@ struct dmrg_ctx {
   // pinned host words for the small per-iteration readbacks (a copy into pageable memory
   // goes through a staging buffer of the driver)
   double* h_words = nullptr;
+  // the FP64 Rayleigh quotient of the mixed path runs on a stream of its own, overlapping
+  // the truncation that follows it (which does not need the energy)
+  cudaStream_t rq_stream = nullptr;
+  cudaEvent_t rq_in = nullptr, rq_out = nullptr;
+  dmrg::DevBuf<double> rq_part;
+  bool rq_pending = false;
   ~dmrg_ctx() {
+    if (rq_stream) {
+      cudaStreamSynchronize(rq_stream);
+      cudaStreamDestroy(rq_stream);
+    }
+    if (rq_in) cudaEventDestroy(rq_in);
+    if (rq_out) cudaEventDestroy(rq_out);
     for (auto e : ev) cudaEventDestroy(e);
     if (h_words) cudaFreeHost(h_words);
   }
@@ -1086,37 +1098,37 @@ static void ensure_two_stage(Ctx& c, Super& sb) {
   sb.two_stage_ready = true;
 }
 
-static void heff(Ctx& c, Super& sb, const double* x, double* y) {
+static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st) {
   // every psi' element is written by exactly one fused tile (blocks without terms get
   // zero-term tiles), so no clearing pass is needed
   const int nb = int(sb.bL.size());
   if (c.opt.precision == DMRG_FP64) {
     c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad64.alloc(sb.pad_size);
-    pad_psi<double>(x, c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
+    pad_psi<double>(x, c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, st);
     HeffPtrs<double> ptr{};
     ptr.L[0] = sb.L.data.p;
     ptr.R[0] = sb.R.data.p;
     ptr.X[0] = c.xpad64.p;
     ptr.Y[0] = y;
     ptr.P[0] = c.part64.p;
-    heff_small<double>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, c.stream);
+    heff_small<double>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
     heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr,
-                       c.stream);
+                       st);
   } else {
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
     c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad32.alloc(sb.pad_size);
-    pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, c.stream);
+    pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, st);
     HeffPtrs<float> ptr{};
     ptr.L[0] = sb.L.data32.p;
     ptr.R[0] = sb.R.data32.p;
     ptr.X[0] = c.xpad32.p;
     ptr.Y[0] = c.f32b.p;
     ptr.P[0] = c.part32.p;
-    heff_small<float>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, c.stream);
-    heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, c.stream);
-    to_f64(c.f32b.p, y, sb.size, c.stream);
+    heff_small<float>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
+    heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, st);
+    to_f64(c.f32b.p, y, sb.size, st);
   }
 }
 
@@ -1138,7 +1150,7 @@ static void heff_timed(Ctx& c, Super& sb, const double* x, double* y) {
     }
   }
   DMRG_CUDA(cudaEventRecord(c.ev[c.ev_used], c.stream));
-  heff(c, sb, x, y);
+  heff(c, sb, x, y, c.stream);
   DMRG_CUDA(cudaEventRecord(c.ev[c.ev_used + 1], c.stream));
   c.ev_used += 2;
   c.heff_products += 1;
@@ -1161,11 +1173,11 @@ static double resolve_heff_timing(Ctx& c) {
 }
 
 // FP64 product regardless of the context precision (energy of the mixed path)
-static void heff64(Ctx& c, Super& sb, const double* x, double* y) {
+static void heff64(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st) {
   int keep = c.opt.precision;
   c.opt.precision = DMRG_FP64;
   try {
-    heff(c, sb, x, y);
+    heff(c, sb, x, y, st);
   } catch (...) {
     c.opt.precision = keep;
     throw;
@@ -1331,12 +1343,27 @@ static void dav_finish(Ctx& c, DavRun& R) {
   dot(c.x.p, c.x.p, n, P.sc + 4, P.part, c.stream);
   scale_vec(c.x.p, n, P.sc + 4, 1, c.stream);
   if (c.opt.precision != DMRG_FP64) {
-    // energy of the mixed path: FP64 Rayleigh quotient of the converged vector
-    heff64(c, sb, c.x.p, c.Ax.p);
-    dot(c.x.p, c.Ax.p, n, P.sc + 5, P.part, c.stream);
-    dav_readback(c, P.sc + 5, 1, h);
-    R.res.theta = h[0];
+    // energy of the mixed path: FP64 Rayleigh quotient of the converged vector, issued on
+    // the context's second stream; dav_energy() waits for it
+    if (!c.rq_stream) {
+      DMRG_CUDA(cudaStreamCreateWithFlags(&c.rq_stream, cudaStreamNonBlocking));
+      DMRG_CUDA(cudaEventCreateWithFlags(&c.rq_in, cudaEventDisableTiming));
+      DMRG_CUDA(cudaEventCreateWithFlags(&c.rq_out, cudaEventDisableTiming));
+    }
+    if (!c.h_words) DMRG_CUDA(cudaMallocHost(&c.h_words, sizeof(double) * 64));
+    c.rq_part.alloc(64 * 300);
+    c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
+    c.xpad64.alloc(sb.pad_size);
+    DMRG_CUDA(cudaEventRecord(c.rq_in, c.stream));
+    DMRG_CUDA(cudaStreamWaitEvent(c.rq_stream, c.rq_in, 0));
+    heff64(c, sb, c.x.p, c.Ax.p, c.rq_stream);
+    dot(c.x.p, c.Ax.p, n, P.sc + 5, c.rq_part.p, c.rq_stream);
+    DMRG_CUDA(cudaMemcpyAsync(c.h_words + 32, P.sc + 5, sizeof(double), cudaMemcpyDeviceToHost,
+                              c.rq_stream));
+    DMRG_CUDA(cudaEventRecord(c.rq_out, c.rq_stream));
+    c.rq_pending = true;
   }
+  (void)h;
   dav_d2d(c, R.out, c.x.p, n);
   if (c.mlp_harvest && R.nhist > 0) harvest(c, sb, R.nhist, c.x.p);
   R.done = true;
@@ -1424,7 +1451,19 @@ static void dav_after_product(Ctx& c, DavRun& R) {
   R.py = avec(R.k);
 }
 
-static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
+// energy of a finished run: the FP64 Rayleigh quotient of the mixed path once it is done
+static void dav_energy(Ctx& c, DavResult& r) {
+  if (!c.rq_pending) return;
+  const double t0 = wall();
+  DMRG_CUDA(cudaEventSynchronize(c.rq_out));
+  c.t_sync += wall() - t0;
+  r.theta = c.h_words[32];
+  c.rq_pending = false;
+}
+
+// defer_energy: leave the Rayleigh quotient of the mixed path running (dav_energy waits)
+static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out,
+                          bool defer_energy = false) {
   PhaseTimer tm(c.t_davidson);
   DavRun R;
   dav_begin(c, sb, guess, out, R);
@@ -1439,6 +1478,7 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out) {
     c.t_detail[19] += 1.0;
   }
   R.res.heff_seconds = resolve_heff_timing(c);
+  if (!defer_energy) dav_energy(c, R.res);
   return R.res;
 }
 
@@ -1780,11 +1820,12 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   c.psi_guess.alloc(std::max<int64_t>(sb.size, 1));
   predict(c, sb, p, dir, c.psi_guess.p);
   c.psi.alloc(std::max<int64_t>(sb.size, 1));
-  DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p);
+  DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p, true);
   const double flops = sb.flops, bytes = sb.bytes;
   c.psi_valid = true;
   c.psi_p = p;
-  TruncResult tr = truncate_renormalize(c, p, dir, M);
+  TruncResult tr = truncate_renormalize(c, p, dir, M);   // overlaps the Rayleigh quotient
+  dav_energy(c, r);
   if (st) {
     st->p = p;
     st->dir = dir;
@@ -1948,7 +1989,7 @@ extern "C" int dmrg_heff_apply(dmrg_ctx* c, int32_t p, const double* x, double* 
     DMRG_REQUIRE(x && y && x != y, DMRG_EINVAL, "bad vectors");
     Super& sb = super_at(*c, p);
     ensure_two_stage(*c, sb);
-    heff(*c, sb, x, y);
+    heff(*c, sb, x, y, c->stream);
     sync(*c);
   });
 }
@@ -2503,6 +2544,7 @@ static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
     c.psi_p = w.p;
     const double flops = c.sb->flops, bytes = c.sb->bytes;
     TruncResult tr = truncate_renormalize(c, w.p, w.dir, w.M);
+    dav_energy(c, runs[w.inst].res);
     dmrg_step_stats& s = st[w.inst];
     s.p = w.p;
     s.dir = w.dir;
