@@ -440,7 +440,8 @@ def run_gpu(args):
         "pool_mallocs": c1["pool_mallocs"] - c0["pool_mallocs"],
         "host_detail_s": [b - a for a, b in zip(c0["t_detail"], c1["t_detail"])],
         "superblock": {k: c1[k] for k in ("sb_blocks_l", "sb_blocks_r", "sb_terms", "sb_tiles",
-                                           "sb_small_tiles", "sb_term_hist")},
+                                           "sb_small_tiles", "sb_term_hist",
+                                           "sb_kernel_flops")},
         "clocks": clocks,
         "energies": [s["energy"] for s in stats],
         "step_ms": step_ms,

@@ -139,6 +139,9 @@ typedef struct {
   int64_t sb_small_tiles;   /* last superblock: tiles of the small-block product kernel */
   int64_t sb_term_hist[8];  /* last superblock: terms whose largest inner dimension is
                                <= 8, <= 16, <= 32, > 32 ([0..3]) and their flops ([4..7]) */
+  double sb_kernel_flops;   /* last superblock: flops of one product in the association the
+                               kernels use (psi R^T first), against the cheaper one counted
+                               in heff_flops */
 } dmrg_counters;
 
 /* Create a context for one problem (Eq. 1 and a target state).  Validates the input

@@ -95,7 +95,8 @@ class Counters(ctypes.Structure):
                 ("sb_blocks_r", ctypes.c_int64), ("sb_terms", ctypes.c_int64),
                 ("sb_tiles", ctypes.c_int64), ("t_detail", ctypes.c_double * 24),
                 ("pool_mallocs", ctypes.c_int64), ("sb_small_tiles", ctypes.c_int64),
-                ("sb_term_hist", ctypes.c_int64 * 8)]
+                ("sb_term_hist", ctypes.c_int64 * 8),
+                ("sb_kernel_flops", ctypes.c_double)]
 
 
 _lib = None

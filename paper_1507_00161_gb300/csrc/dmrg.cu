@@ -161,7 +161,8 @@ struct dmrg_ctx {
          t_predict = 0;
   double t_sync = 0, t_enlarge_host = 0;   // host blocked on the stream; enlarge host walk
   int64_t last_sizes[5] = {0, 0, 0, 0, 0};   // last superblock: L, R blocks, terms, tiles, small tiles
-  int64_t term_hist[8] = {};   // last superblock: terms by largest inner dim; flops share
+  int64_t term_hist[8] = {};
+  double kernel_flops = 0;     // last superblock: flops in the order the tile kernels use   // last superblock: terms by largest inner dim; flops share
   double t_detail[24] = {};   // finer host phases (see dmrg.h)
   dmrg::Chain chain;
   dmrg::MPO mpo;
@@ -871,7 +872,7 @@ static void build_super(Ctx& c, int p) {
   std::vector<HeffItem> fi(i_beg[nb]);
   std::vector<TileCost> ft(t_beg[nb]), fts(s_beg[nb]);
   std::vector<HeffRed> fr(r_beg[nb]);
-  std::vector<double> bo_flops(nb, 0.0), bo_bytes(nb, 0.0);
+  std::vector<double> bo_flops(nb, 0.0), bo_bytes(nb, 0.0), bo_kflops(nb, 0.0);
   std::vector<int64_t> bo_toff(nb, 0);
   std::vector<std::array<double, 8>> bo_hist(nb);
   sb->terms_host.resize(i_beg[nb]);
@@ -879,7 +880,7 @@ static void build_super(Ctx& c, int p) {
     for (int bo = b0; bo < b1; ++bo) {
       const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
       const int i0 = int(i_beg[bo]), i1 = int(i_beg[bo + 1]);
-      double work = 0, fl = 0, by = 0;
+      double work = 0, fl = 0, by = 0, kfl = 0;
       std::array<double, 8> hist{};
       int64_t to = 0;
       for (int j = i0; j < i1; ++j) {
@@ -904,9 +905,11 @@ static void build_super(Ctx& c, int p) {
         const int cls = dmax <= 8 ? 0 : dmax <= 16 ? 1 : dmax <= 32 ? 2 : 3;
         hist[cls] += 1.0;
         hist[4 + cls] += std::min(f1, f2);
+        kfl += f1;   // the tile kernels form psi R^T first
         sb->terms_host[j] = Super::Term{it.lb, it.rb, it.bin, it.bout, it.sign};
       }
       bo_flops[bo] = fl;
+      bo_kflops[bo] = kfl;
       bo_bytes[bo] = by;
       bo_hist[bo] = hist;
       bo_toff[bo] = to;
@@ -960,6 +963,8 @@ static void build_super(Ctx& c, int p) {
     for (int i = 0; i < 8; ++i) hist[i] += bo_hist[bo][i];
   }
   for (int i = 0; i < 8; ++i) c.term_hist[i] = int64_t(hist[i]);
+  c.kernel_flops = 0;
+  for (int bo = 0; bo < nb; ++bo) c.kernel_flops += bo_kflops[bo];
   const int64_t items = i_beg[nb];
   const int64_t pelems = p_beg[nb];
   sb->t_elems = toff;
@@ -2133,6 +2138,7 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->sb_tiles = c->last_sizes[3];
     out->sb_small_tiles = c->last_sizes[4];
     for (int i = 0; i < 8; ++i) out->sb_term_hist[i] = c->term_hist[i];
+    out->sb_kernel_flops = c->kernel_flops;
     for (int i = 0; i < 24; ++i) out->t_detail[i] = c->t_detail[i];
     out->t_detail[15] = 1e-9 * double(g_malloc_ns.load());
     out->pool_mallocs = g_malloc_count.load();

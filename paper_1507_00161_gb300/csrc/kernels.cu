@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "common.h"
 
@@ -660,12 +661,19 @@ __device__ void sort_and_fix(const double* A, const double* V, int n, double* w_
   }
 }
 
+// Matrices up to kEighSmem on a side are decomposed in shared memory (the rotations touch
+// every element of two rows and two columns per round); larger ones in their global
+// workspace.
+constexpr int kEighSmem = 64;
+constexpr size_t kEighSmemBytes = sizeof(double) * 2 * kEighSmem * kEighSmem;
+
 // w offsets are provided separately to keep the kernel general
 __global__ void __launch_bounds__(256) k_batched_eigh2(const int64_t* __restrict__ off,
                                                        const int64_t* __restrict__ woff,
                                                        const int32_t* __restrict__ dim,
                                                        double* A, double* V, double* Vs,
                                                        double* w, int descending, int clip) {
+  extern __shared__ double eigh_sm[];
   __shared__ double cs[1024];
   __shared__ int pp[512], qq[512];
   __shared__ double red[80];
@@ -673,26 +681,46 @@ __global__ void __launch_bounds__(256) k_batched_eigh2(const int64_t* __restrict
   int n = dim[s];
   if (n <= 0) return;
   int64_t o = off[s];
-  jacobi_block(A + o, V + o, n, cs, pp, qq, red);
+  double* Aw = A + o;
+  double* Vw = V + o;
+  if (n <= kEighSmem) {
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) eigh_sm[i] = Aw[i];
+    Aw = eigh_sm;
+    Vw = eigh_sm + n * n;
+    __syncthreads();
+  }
+  jacobi_block(Aw, Vw, n, cs, pp, qq, red);
   __syncthreads();
-  sort_and_fix(A + o, V + o, n, w + woff[s], Vs + o, descending, clip, n, 1);
+  sort_and_fix(Aw, Vw, n, w + woff[s], Vs + o, descending, clip, n, 1);
+}
+
+static void eigh_smem_attr() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    DMRG_CUDA(cudaFuncSetAttribute(k_batched_eigh2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(kEighSmemBytes)));
+  });
 }
 
 void batched_eigh2(const int64_t* d_off, const int64_t* d_woff, const int32_t* d_dim, int n,
                    double* d_A, double* d_V, double* d_Vs, double* d_w, int descending, int clip,
                    cudaStream_t s) {
   if (n <= 0) return;
-  k_batched_eigh2<<<n, 256, 0, s>>>(d_off, d_woff, d_dim, d_A, d_V, d_Vs, d_w, descending, clip);
+  eigh_smem_attr();
+  k_batched_eigh2<<<n, 256, kEighSmemBytes, s>>>(d_off, d_woff, d_dim, d_A, d_V, d_Vs, d_w,
+                                                  descending, clip);
   DMRG_LAUNCHED();
 }
 
 // Ritz problem: H (k x k, leading dimension ld) -> ascending eigenvalues w, eigenvectors Y
-// (k x k, column j = j-th lowest, sign fixed)
-__global__ void k_ritz(const double* __restrict__ H, int ld, int k, double* A, double* V,
-                       double* w, double* Y) {
+// (k x k, column j = j-th lowest, sign fixed); k <= 64, decomposed in shared memory
+__global__ void k_ritz(const double* __restrict__ H, int ld, int k, double* w, double* Y) {
+  extern __shared__ double ritz_sm[];
   __shared__ double cs[1024];
   __shared__ int pp[512], qq[512];
   __shared__ double red[80];
+  double* A = ritz_sm;
+  double* V = ritz_sm + k * k;
   for (int i = threadIdx.x; i < k * k; i += blockDim.x) {
     int r = i / k, c = i - r * k;
     // symmetric from the lower triangle: row j holds <v_i, H v_j> for i <= j
@@ -707,7 +735,14 @@ __global__ void k_ritz(const double* __restrict__ H, int ld, int k, double* A, d
 
 void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w, double* d_Y,
                 cudaStream_t s) {
-  k_ritz<<<1, 256, 0, s>>>(d_H, ld, k, d_scratch, d_scratch + 64 * 64, d_w, d_Y);
+  (void)d_scratch;
+  DMRG_REQUIRE(k >= 1 && k <= kEighSmem, DMRG_EINVAL, "internal: Ritz problem too large");
+  static std::once_flag once;
+  std::call_once(once, [] {
+    DMRG_CUDA(cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(kEighSmemBytes)));
+  });
+  k_ritz<<<1, 256, sizeof(double) * 2 * k * k, s>>>(d_H, ld, k, d_w, d_Y);
   DMRG_LAUNCHED();
 }
 
