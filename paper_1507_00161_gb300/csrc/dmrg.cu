@@ -110,6 +110,28 @@ struct Blk {
   OpSet ops;
   Iso iso;
   bool valid = false;
+  uint64_t gen = 0;   // changes whenever ops change (identifies the block for prefetching)
+};
+
+// host part of an enlargement: layout, destination block table, device tables to upload
+struct EnlPlan {
+  Layout lay;
+  OpSet out;                                   // host tables only, no data
+  std::vector<std::vector<EnlBlock>> part;     // destination blocks in label order
+  std::vector<int64_t> pbase;
+  std::vector<LayDev> ld;
+  double det[8] = {};                          // host seconds of its phases
+};
+
+// enlargement planned ahead on a host thread while the GPU works on the previous step
+struct Prefetch {
+  std::thread th;
+  bool active = false;
+  int s = -1;
+  bool left = false;
+  uint64_t gen = 0;
+  EnlPlan plan;
+  std::exception_ptr err;
 };
 
 struct Super {
@@ -173,6 +195,7 @@ struct dmrg_ctx {
   std::vector<dmrg::Blk> left, right;
   bool built = false;
   std::unique_ptr<dmrg::Super> sb;
+  dmrg::Prefetch pf;
   // Davidson workspace
   dmrg::DevBuf<double> V, AV, r, t, x, Ax, x1, Ax1, small, partials;
   dmrg::DevBuf<const double*> vptr;
@@ -215,6 +238,7 @@ struct dmrg_ctx {
   dmrg::DevBuf<double> rq_part;
   bool rq_pending = false;
   ~dmrg_ctx() {
+    if (pf.th.joinable()) pf.th.join();
     if (rq_stream) {
       cudaStreamSynchronize(rq_stream);
       cudaStreamDestroy(rq_stream);
@@ -229,6 +253,8 @@ struct dmrg_ctx {
 namespace dmrg {
 
 thread_local Pool* tl_pool = nullptr;
+
+static std::atomic<uint64_t> g_blk_gen{0};   // generations of stored blocks
 
 using Ctx = dmrg_ctx;
 
@@ -468,23 +494,23 @@ static void parallel_for(int n, F&& fn, int grain = 16) {
   pool.run(nt, job);
 }
 
-static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& out) {
-  PhaseTimer tm(c.t_enlarge);
-  const double th0 = wall();
-  double te = th0;
+// Host part of the enlargement of blk by site s: reads the context and blk only (the site
+// entries of s must be ready), so it may run on another host thread.
+static void plan_enlarge(const Ctx& c, const OpSet& blk, int s, bool left, EnlPlan& P) {
+  double te = wall();
   auto elap = [&](int i) {
     const double t = wall();
-    c.t_detail[i] += t - te;
+    P.det[i - 8] += t - te;
     te = t;
   };
+  Layout& lay = P.lay;
+  OpSet& out = P.out;
   make_layout(c, blk.sec, s, left, lay);
-  ensure_site_entries(c, s, left);
   elap(8);
-  ensure_dev_index(c, blk);
-  elap(9);
   const SiteEntries& se = left ? c.ent_left[s] : c.ent_right[s];
   const int nE = lay.sec.size();
   const int nsrc = blk.sec.size();
+  (void)nsrc;
   const int ndst = int(se.ptr.size()) - 1;
   const auto& dq = left ? c.mpo.dq[s + 1] : c.mpo.dq[s];
   // destination blocks (label k, Q_in) that receive at least one contribution, with
@@ -535,7 +561,8 @@ static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& ou
       }
   }, 2);
   elap(10);
-  std::vector<std::vector<EnlBlock>> part(16);
+  std::vector<std::vector<EnlBlock>>& part = P.part;
+  part.assign(16, {});
   std::vector<int64_t> part_elems(16, 0);
   parallel_for(ndst, [&](int k0, int k1, int t) {
     auto& v = part[t];
@@ -569,7 +596,9 @@ static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& ou
   // the fused product), i.e. block b starts at the sum of the rounded-up sizes before it.
   // Threads own increasing label ranges, so concatenating their lists keeps label order.
   const int nparts = int(part.size());
-  std::vector<int64_t> pbase(nparts + 1, 0), pelem(nparts + 1, 0);
+  std::vector<int64_t>& pbase = P.pbase;
+  pbase.assign(nparts + 1, 0);
+  std::vector<int64_t> pelem(nparts + 1, 0);
   for (int t = 0; t < nparts; ++t) {
     pbase[t + 1] = pbase[t] + int64_t(part[t].size());
     pelem[t + 1] = pelem[t] + part_elems[t];
@@ -593,34 +622,97 @@ static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& ou
   for (int k = 0; k < ndst; ++k) out.lab_ptr[k + 1] += out.lab_ptr[k];
   out.n_elems = pelem[nparts];
   elap(12);
+  // device tables and the index by input sector (host)
+  P.ld.resize(nE);
+  for (int i = 0; i < nE; ++i)
+    P.ld[i] = LayDev{lay.pblk[i][0], lay.pblk[i][1], lay.poff[i][1], lay.sec.d[i]};
+  out.index_by_in();
+  elap(14);
+}
+
+// Device part: the arena, the tables, the kernel (context stream, waited for).
+static void exec_enlarge(Ctx& c, OpSet& blk, int s, bool left, EnlPlan& P, Layout& lay,
+                         OpSet& out) {
+  double te = wall();
+  ensure_dev_index(c, blk);
+  c.t_detail[9] += wall() - te;
+  const SiteEntries& se = left ? c.ent_left[s] : c.ent_right[s];
+  lay = std::move(P.lay);
+  out = std::move(P.out);
   out.data.alloc(out.n_elems + 4);
-  elap(13);
-  // layout table for the device
-  std::vector<LayDev> ld(nE);
-  for (int i = 0; i < nE; ++i) ld[i] = LayDev{lay.pblk[i][0], lay.pblk[i][1], lay.poff[i][1], lay.sec.d[i]};
+  const int nparts = int(P.part.size());
   DevBuf<LayDev> dlay;
   DevBuf<EnlBlock> deb;
-  dlay.upload(ld, c.stream);
-  deb.alloc(std::max<int64_t>(pbase[nparts], 1));
+  dlay.upload(P.ld, c.stream);
+  deb.alloc(std::max<int64_t>(P.pbase[nparts], 1));
   for (int t = 0; t < nparts; ++t)
-    if (!part[t].empty())
-      DMRG_CUDA(cudaMemcpyAsync(deb.p + pbase[t], part[t].data(), sizeof(EnlBlock) * part[t].size(),
-                                cudaMemcpyHostToDevice, c.stream));
-  const int64_t n_eb = pbase[nparts];
+    if (!P.part[t].empty())
+      DMRG_CUDA(cudaMemcpyAsync(deb.p + P.pbase[t], P.part[t].data(),
+                                sizeof(EnlBlock) * P.part[t].size(), cudaMemcpyHostToDevice,
+                                c.stream));
+  const int64_t n_eb = P.pbase[nparts];
   const auto& spar = left ? c.mpo.parity[s] : c.mpo.parity[s + 1];
-  elap(14);
-  c.t_enlarge_host += wall() - th0;
   DevBuf<int8_t> dpar;
   dpar.upload(spar, c.stream);
-  enlarge_blocks(deb.p, n_eb, se.dptr.p, se.de.p, blk.d_by_in.p, nsrc, blk.d_boff.p,
+  enlarge_blocks(deb.p, n_eb, se.dptr.p, se.de.p, blk.d_by_in.p, blk.sec.size(), blk.d_boff.p,
                  blk.d_dim.p, blk.d_npart.p, dpar.p, dlay.p, left ? 1 : 0, blk.data.p,
                  out.data.p, c.stream);
-  double tp = wall();
+  te = wall();
   sync(c);   // the small tables above are released
-  c.t_detail[7] += wall() - tp;
-  tp = wall();
-  out.index_by_in();
-  c.t_detail[6] += wall() - tp;
+  c.t_detail[7] += wall() - te;
+}
+
+static void wait_prefetch(Ctx& c) {
+  if (c.pf.th.joinable()) c.pf.th.join();
+}
+
+// a finished plan for (blk, s, left) if one was prefetched
+static bool take_prefetch(Ctx& c, uint64_t gen, int s, bool left, EnlPlan& P) {
+  if (!c.pf.active || c.pf.s != s || c.pf.left != left) return false;   // kept for later
+  wait_prefetch(c);
+  c.pf.active = false;
+  const bool hit = !c.pf.err && c.pf.s == s && c.pf.left == left && c.pf.gen == gen;
+  if (hit) P = std::move(c.pf.plan);
+  c.pf.plan = EnlPlan();
+  c.pf.err = nullptr;
+  return hit;
+}
+
+// plan the enlargement of blk by site s on a host thread (gen: blk's generation)
+static void start_prefetch(Ctx& c, const OpSet& blk, uint64_t gen, int s, bool left) {
+  wait_prefetch(c);
+  ensure_site_entries(c, s, left);   // main thread: may upload
+  c.pf.active = true;
+  c.pf.s = s;
+  c.pf.left = left;
+  c.pf.gen = gen;
+  c.pf.plan = EnlPlan();
+  c.pf.err = nullptr;
+  const Ctx* cc = &c;
+  const OpSet* src = &blk;
+  Prefetch* pf = &c.pf;
+  c.pf.th = std::thread([cc, src, s, left, pf] {
+    try {
+      plan_enlarge(*cc, *src, s, left, pf->plan);
+    } catch (...) {
+      pf->err = std::current_exception();
+    }
+  });
+}
+
+// operators of the enlarged space; blk_gen identifies blk for a prefetched plan (0: none)
+static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& out,
+                    uint64_t blk_gen = 0) {
+  PhaseTimer tm(c.t_enlarge);
+  const double th0 = wall();
+  EnlPlan P;
+  if (!(blk_gen && take_prefetch(c, blk_gen, s, left, P))) {
+    ensure_site_entries(c, s, left);
+    plan_enlarge(c, blk, s, left, P);
+    for (int i = 0; i < 8; ++i) c.t_detail[8 + i] += P.det[i];
+  }
+  c.t_enlarge_host += wall() - th0;
+  exec_enlarge(c, blk, s, left, P, lay, out);
 }
 
 // stored block = kept part of an enlarged operator set: O' = U_o^T O U_i per block
@@ -762,8 +854,8 @@ static void build_super(Ctx& c, int p) {
                "blocks for this position are not available");
   auto sb = std::make_unique<Super>();
   sb->p = p;
-  enlarge(c, c.left[p - 1].ops, p, true, sb->Ll, sb->L);
-  enlarge(c, c.right[p + 1].ops, p + 1, false, sb->Rl, sb->R);
+  enlarge(c, c.left[p - 1].ops, p, true, sb->Ll, sb->L, c.left[p - 1].gen);
+  enlarge(c, c.right[p + 1].ops, p + 1, false, sb->Rl, sb->R, c.right[p + 1].gen);
   const QN T = c.chain.target;
   const int nL = sb->Ll.sec.size(), nR = sb->Rl.sec.size();
   sb->psi_of_L.assign(nL, -1);
@@ -1497,6 +1589,7 @@ struct TruncResult {
 };
 
 static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
+  wait_prefetch(c);   // a plan being made reads stored blocks; this changes one
   PhaseTimer tm(c.t_truncate);
   DMRG_REQUIRE(c.sb && c.sb->p == p && c.psi_valid && c.psi_p == p, DMRG_EINVAL,
                "no eigenvector held for this position (call dmrg_davidson first)");
@@ -1601,6 +1694,7 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
   dst.ops = std::move(ops);
   dst.iso = std::move(iso);
   dst.valid = true;
+  dst.gen = ++g_blk_gen;
   c.prev = std::move(c.sb);   // layouts of the superblock psi belongs to
   return tr;
 }
@@ -1737,6 +1831,8 @@ static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
 // blocks from the starting state
 // ---------------------------------------------------------------------------------------
 static void build_blocks(Ctx& c, const dmrg_mps_init* init) {
+  wait_prefetch(c);
+  c.pf.active = false;
   const int N = c.N;
   cudaStream_t s = c.stream;
   c.left.clear();
@@ -1755,6 +1851,7 @@ static void build_blocks(Ctx& c, const dmrg_mps_init* init) {
     identity_iso(c, lay, c.left[0].iso);
     project(c, E, c.left[0].iso, c.left[0].ops);
     c.left[0].valid = true;
+    c.left[0].gen = ++g_blk_gen;
   }
   {
     OpSet vac = vacuum_ops(int(c.mpo.labels[N].size()), 0, s);
@@ -1764,6 +1861,7 @@ static void build_blocks(Ctx& c, const dmrg_mps_init* init) {
     identity_iso(c, lay, c.right[N - 2].iso);
     project(c, E, c.right[N - 2].iso, c.right[N - 2].ops);
     c.right[N - 2].valid = true;
+    c.right[N - 2].gen = ++g_blk_gen;
   }
   DMRG_REQUIRE(init != nullptr, DMRG_EINVAL, "starting state is NULL");
   DMRG_REQUIRE(init->n_bonds == N - 4, DMRG_EINVAL, "starting state must cover bonds N-3..2");
@@ -1808,6 +1906,7 @@ static void build_blocks(Ctx& c, const dmrg_mps_init* init) {
     c.right[b].ops = std::move(ops);
     c.right[b].iso = std::move(iso);
     c.right[b].valid = true;
+    c.right[b].gen = ++g_blk_gen;
   }
   c.built = true;
 }
@@ -1822,6 +1921,12 @@ static double now_s() {
 static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   double t0 = now_s();
   Super& sb = super_at(c, p);
+  // the block that the next step of this sweep enlarges on the side this step leaves as
+  // it is: plan its enlargement on a host thread while the GPU runs this step
+  if (dir == 0 && p + 2 <= c.N - 2 && c.right[p + 2].valid)
+    start_prefetch(c, c.right[p + 2].ops, c.right[p + 2].gen, p + 2, false);
+  else if (dir == 1 && p - 2 >= 0 && c.left[p - 2].valid)
+    start_prefetch(c, c.left[p - 2].ops, c.left[p - 2].gen, p - 1, true);
   c.psi_guess.alloc(std::max<int64_t>(sb.size, 1));
   predict(c, sb, p, dir, c.psi_guess.p);
   c.psi.alloc(std::max<int64_t>(sb.size, 1));
