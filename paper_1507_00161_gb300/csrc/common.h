@@ -458,6 +458,7 @@ void project_blocks(const ProjTask* tasks, const int64_t* tile_beg1, int64_t n_t
                     const int32_t* m, const int64_t* uoff, const double* X, const double* U,
                     double* T, double* Y, cudaStream_t s);
 // blocks with D_o, D_i <= 32 (one warp each, both products fused)
+void set_ones(double* x, const int64_t* pos, int64_t n, cudaStream_t s);
 void project_small(const ProjTask* tasks, int64_t n, const int32_t* D, const int32_t* m,
                    const int64_t* uoff, const double* X, const double* U, double* Y,
                    cudaStream_t s);

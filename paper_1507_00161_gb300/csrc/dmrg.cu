@@ -719,8 +719,8 @@ static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& ou
 static void project(Ctx& c, OpSet& E, const Iso& iso, OpSet& out) {
   PhaseTimer tm(c.t_project);
   if (iso.identity) {
-    out = std::move(E);
-    out.index_by_in();
+    out = std::move(E);   // its index by input sector was built with it
+    out.dev_index_ready = false;
     return;
   }
   const int nE = E.sec.size();
@@ -802,7 +802,6 @@ static void identity_iso(Ctx& c, const Layout& lay, Iso& iso) {
   iso.uoff.assign(n, 0);
   iso.kept_idx.resize(n);
   iso.enl_idx.resize(n);
-  std::vector<double> h;
   int64_t off = 0;
   for (int i = 0; i < n; ++i) {
     iso.kept_idx[i] = i;
@@ -810,10 +809,17 @@ static void identity_iso(Ctx& c, const Layout& lay, Iso& iso) {
     iso.uoff[i] = off;
     off += int64_t(lay.sec.d[i]) * lay.sec.d[i];
   }
-  h.assign(off, 0.0);
+  // zeros, then ones at the diagonal positions (built on the device)
+  std::vector<int64_t> diag;
+  diag.reserve(size_t(lay.sec.total()));
   for (int i = 0; i < n; ++i)
-    for (int r = 0; r < lay.sec.d[i]; ++r) h[iso.uoff[i] + int64_t(r) * lay.sec.d[i] + r] = 1.0;
-  iso.data.upload(h, c.stream);
+    for (int r = 0; r < lay.sec.d[i]; ++r) diag.push_back(iso.uoff[i] + int64_t(r) * lay.sec.d[i] + r);
+  iso.data.alloc(std::max<int64_t>(off, 1));
+  DMRG_CUDA(cudaMemsetAsync(iso.data.p, 0, sizeof(double) * std::max<int64_t>(off, 1), c.stream));
+  DevBuf<int64_t> dd;
+  dd.upload(diag, c.stream);
+  set_ones(iso.data.p, dd.p, int64_t(diag.size()), c.stream);
+  sync(c);   // dd is released
   iso.identity = true;
 }
 

@@ -361,6 +361,18 @@ void enlarge_blocks(const EnlBlock* blocks, int64_t n, const int32_t* eptr, cons
   DMRG_LAUNCHED();
 }
 
+// x[pos[i]] = 1 (identity isometries)
+__global__ void k_set_ones(double* __restrict__ x, const int64_t* __restrict__ pos, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    x[pos[i]] = 1.0;
+}
+void set_ones(double* x, const int64_t* pos, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_set_ones<<<int(std::min<int64_t>((n + 255) / 256, 1024)), 256, 0, s>>>(x, pos, n);
+  DMRG_LAUNCHED();
+}
+
 // ------------------------------------------------------------------------------------
 // vector kernels
 // ------------------------------------------------------------------------------------
@@ -749,8 +761,13 @@ void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w
 // ------------------------------------------------------------------------------------
 // selection: k-th largest of w[0..n) by a descending bitonic sort in one block
 // ------------------------------------------------------------------------------------
-__global__ void k_kth_largest(const double* __restrict__ w, int64_t n, int64_t k, double* buf,
+// bitonic sort (descending) of w padded to np2 with -inf, in shared memory when it fits
+constexpr int64_t kKthSmem = 16384;
+
+__global__ void k_kth_largest(const double* __restrict__ w, int64_t n, int64_t k, double* gbuf,
                               int64_t np2, double* out) {
+  extern __shared__ double kth_sm[];
+  double* buf = np2 <= kKthSmem ? kth_sm : gbuf;
   for (int64_t i = threadIdx.x; i < np2; i += blockDim.x) buf[i] = i < n ? w[i] : -INFINITY;
   __syncthreads();
   for (int64_t size = 2; size <= np2; size <<= 1) {
@@ -771,12 +788,17 @@ __global__ void k_kth_largest(const double* __restrict__ w, int64_t n, int64_t k
   }
   if (threadIdx.x == 0) out[0] = buf[k - 1];
 }
-
 void kth_largest(const double* w, int64_t n, int64_t k, double* d_scratch, double* out,
                  cudaStream_t s) {
   int64_t np2 = 1;
   while (np2 < n) np2 <<= 1;
-  k_kth_largest<<<1, 1024, 0, s>>>(w, n, k, d_scratch, np2, out);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    DMRG_CUDA(cudaFuncSetAttribute(k_kth_largest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(sizeof(double) * kKthSmem)));
+  });
+  const size_t smem = np2 <= kKthSmem ? sizeof(double) * size_t(np2) : 0;
+  k_kth_largest<<<1, 1024, smem, s>>>(w, n, k, d_scratch, np2, out);
   DMRG_LAUNCHED();
 }
 
