@@ -172,23 +172,46 @@ __global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 4 : 2)
     const T* Ls = ring + slot_pos[warp][done % kDepth];
     const T* Rs = Ls + round_vec<T>(m * dLi);
     const T* Ps = Rs + round_vec<T>(n * dRi);
-    if (act) {
-      const T* rr = Rs + c * dRi;
-      for (int i = g; i < dLi; i += G) {
-        const T* pr = Ps + i * dRi;
-        T s = T(0);
-        for (int r = 0; r < dRi; ++r) s = fma(pr[r], rr[r], s);
-        Xs[i * (kT + 1) + c] = s;
+    // the cheaper association of L psi R^T for this tile: (psi R^T) first or (L psi) first
+    const bool lfirst = int64_t(m) * dRi * (dLi + n) < int64_t(n) * dLi * (dRi + m);
+    if (!lfirst) {
+      if (act) {
+        const T* rr = Rs + c * dRi;
+        for (int i = g; i < dLi; i += G) {
+          const T* pr = Ps + i * dRi;
+          T s = T(0);
+          for (int r = 0; r < dRi; ++r) s = fma(pr[r], rr[r], s);
+          Xs[i * (kT + 1) + c] = s;
+        }
       }
-    }
-    __syncwarp();
-    if (act) {
-      const T* lr = Ls + g * dLi;
-      for (int k = 0; k < dLi; ++k) {
-        const T xv = sg * Xs[k * (kT + 1) + c];
+      __syncwarp();
+      if (act) {
+        const T* lr = Ls + g * dLi;
+        for (int k = 0; k < dLi; ++k) {
+          const T xv = sg * Xs[k * (kT + 1) + c];
 #pragma unroll
-        for (int q = 0; q < kT; ++q)
-          if (q < rows_mine) acc[q] = fma(lr[q * G * dLi + k], xv, acc[q]);
+          for (int q = 0; q < kT; ++q)
+            if (q < rows_mine) acc[q] = fma(lr[q * G * dLi + k], xv, acc[q]);
+        }
+      }
+    } else {
+      // Z (m x dRi) = L psi in shared memory, then acc[i][c] += s sum_b Z[i][b] R[c][b]
+      for (int e = lane; e < m * dRi; e += 32) {
+        const int i = e / dRi, b = e - i * dRi;
+        const T* lr = Ls + i * dLi;
+        T s = T(0);
+        for (int a = 0; a < dLi; ++a) s = fma(lr[a], Ps[a * dRi + b], s);
+        Xs[i * (kT + 1) + b] = s;
+      }
+      __syncwarp();
+      if (act) {
+        const T* rr = Rs + c * dRi;
+        for (int b = 0; b < dRi; ++b) {
+          const T rv = sg * rr[b];
+#pragma unroll
+          for (int q = 0; q < kT; ++q)
+            if (q < rows_mine) acc[q] = fma(Xs[(g + q * G) * (kT + 1) + b], rv, acc[q]);
+        }
       }
     }
     __syncwarp();
