@@ -280,6 +280,47 @@ def run_batch_compare(P, M_cap):
                         "M=128*2^(i mod 5) capped at %d, seeds 1000+i, mixed path" % M_cap}
 
 
+def run_precond_compare(P):
+    """Learned vs diagonal Davidson preconditioner: harvest two sweeps of sd 4p+4n at
+    M = 256, train the network on the GPU (20 epochs), then Davidson from the uniform guess at every
+    position of one sweep with each preconditioner (same converged energies)."""
+    import torch
+    from gen import make_problem, initial_mps
+    prob = make_problem("sd", 4, 4, 0, seed=1)
+    d = P.DMRG(prob, precision=P.MIXED_FP32)
+    d.build_blocks(initial_mps(prob, 256, 5))
+    t0 = time.perf_counter()
+    d.mlp_harvest(True, 2048)
+    d.sweep(256)
+    d.sweep(256)
+    d.mlp_harvest(False)
+    d.mlp_reset(3)
+    loss0, ns = d.mlp_train(epochs=1, batch=1024, lr=1e-3, seed=3)
+    loss1, _ = d.mlp_train(epochs=20, batch=1024, lr=1e-3, seed=4)
+    t_train = time.perf_counter() - t0
+    n_diag = n_mlp = 0
+    dmax = 0.0
+    N = prob.n_sites
+    for p in range(1, N - 2):
+        size = d.psi_layout(p)["size"]
+        x0 = torch.ones(size, dtype=torch.float64, device="cuda")
+        d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
+        e1, s1 = d.davidson(p, guess=x0, allow_noconv=True)
+        d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_MLP)
+        e2, s2 = d.davidson(p, guess=x0, allow_noconv=True)
+        n_diag += s1["n_products"]
+        n_mlp += s2["n_products"]
+        dmax = max(dmax, abs(e1 - e2))
+        d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
+        d.step(p, 0, 256)
+    d.close()
+    return {"workload": "sd 4p+4n seed 1, M=256, two harvested sweeps, 20 epochs; Davidson from "
+                        "the uniform guess at positions 1..%d, mixed path" % (N - 3),
+            "samples": ns, "loss": [loss0, loss1], "train_s": t_train,
+            "products_diagonal": n_diag, "products_learned": n_mlp,
+            "max_dE": dmax}
+
+
 def run_gpu(args):
     import ctypes
     import numpy as np
@@ -401,6 +442,7 @@ def run_gpu(args):
     batch = None
     if args.batch_mcap > 0:
         batch = run_batch_compare(P, args.batch_mcap)
+    precond = run_precond_compare(P) if args.precond else None
     if rank != 0:
         return 0
     cpu = None
@@ -430,6 +472,7 @@ def run_gpu(args):
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "batch": batch,
+        "precond": precond,
         "e2e": e2e,
         "gpu_launches": int(c1["launches"] - c0["launches"]),
         "device_mem_used_gb": dev_used_gb,
@@ -464,6 +507,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-mcap", type=int, default=256,
                     help="M cap of the 32-instance batch-vs-loop comparison (0: skip)")
+    ap.add_argument("--precond", type=int, default=1,
+                    help="learned vs diagonal preconditioner comparison (0: skip)")
     ap.add_argument("--workload", default="",
                     help="space:Np:Nn:seed of another system (profiling of smaller cases)")
     ap.add_argument("--profile-range", action="store_true",

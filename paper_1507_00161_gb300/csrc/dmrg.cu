@@ -1356,7 +1356,8 @@ static void harvest(Ctx& c, Super& sb, int nhist, const double* psi) {
     mlp_harvest(rh, xh, psi, sb.diag.p, sc, n, start, stride, cnt,
                 c.mlp_samples.p + c.mlp_head * 5, s);
     c.mlp_head += cnt;
-    c.mlp_nsamp = std::min<int64_t>(c.mlp_cap, c.mlp_nsamp + cnt);
+    // filled prefix of the ring: the slots beyond the furthest write were never written
+    c.mlp_nsamp = std::max<int64_t>(c.mlp_nsamp, c.mlp_head);
   }
   ++c.mlp_calls;
 }

@@ -126,6 +126,12 @@ __global__ void k_gather(const T* __restrict__ S, const int32_t* __restrict__ id
 // features of every element of a Davidson iterate:
 //   asinh(theta - D_i), r_i sqrt(n)/|r|, x_i sqrt(n), d_i sqrt(n)/|d|,  d_i = r_i/(theta - D_i)
 // (the clamped diagonal correction); sc = {theta, |r|^2, |d|^2}
+// features and targets are O(1) by construction; bound the rare outliers (an element whose
+// diagonal sits on theta, a residual at rounding level) so that FP32 training stays finite
+__device__ __forceinline__ float clampf(double v) {
+  return float(v != v ? 0.0 : fmin(fmax(v, -1e4), 1e4));
+}
+
 template <class T>
 __global__ void k_features(const double* __restrict__ r, const double* __restrict__ x,
                            const double* __restrict__ diag, const double* __restrict__ sc,
@@ -138,10 +144,10 @@ __global__ void k_features(const double* __restrict__ r, const double* __restric
        i += int64_t(gridDim.x) * blockDim.x) {
     double den = th - diag[i];
     if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
-    X[i * kIn + 0] = T(asinh(th - diag[i]));
-    X[i * kIn + 1] = T(r[i] * ir);
-    X[i * kIn + 2] = T(x[i] * sn);
-    X[i * kIn + 3] = T(r[i] / den * id);
+    X[i * kIn + 0] = T(clampf(asinh(th - diag[i])));
+    X[i * kIn + 1] = T(clampf(r[i] * ir));
+    X[i * kIn + 2] = T(clampf(x[i] * sn));
+    X[i * kIn + 3] = T(clampf(r[i] / den * id));
   }
 }
 
@@ -158,18 +164,20 @@ __global__ void k_harvest(const double* __restrict__ r, const double* __restrict
   const double id = sc[2] > 0 ? sn / sqrt(sc[2]) : 0.0;
   const double ov = sc[3];
   const double sg = ov < 0 ? -1.0 : 1.0;
-  const double ie = sc[4] > 0 ? sn / sqrt(sc[4]) : 0.0;
+  // an iterate that already equals the eigenvector (|e| at rounding level) has no error
+  // direction to learn: its targets are zero
+  const double ie = sc[4] > 1e-20 ? sn / sqrt(sc[4]) : 0.0;
   for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < count;
        k += int64_t(gridDim.x) * blockDim.x) {
     const int64_t i = start + k * stride;
     double den = th - diag[i];
     if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
     float* o = out + k * (kIn + 1);
-    o[0] = float(asinh(th - diag[i]));
-    o[1] = float(r[i] * ir);
-    o[2] = float(x[i] * sn);
-    o[3] = float(r[i] / den * id);
-    o[4] = float(sg * (psi[i] - x[i] * ov) * ie);
+    o[0] = clampf(asinh(th - diag[i]));
+    o[1] = clampf(r[i] * ir);
+    o[2] = clampf(x[i] * sn);
+    o[3] = clampf(r[i] / den * id);
+    o[4] = clampf(sg * (psi[i] - x[i] * ov) * ie);
   }
 }
 

@@ -62,3 +62,23 @@ def test_trained_preconditioner_same_energies(P, capsys):
     with capsys.disabled():
         print(f"\n[learned preconditioner] sd 2p+2n M=64, positions 2..11 from the uniform guess: "
               f"diagonal {n_diag} products, learned {n_mlp} products (loss {loss0:.3f} -> {loss1:.3f})")
+    # what the trained network gains: fewer H_eff products for the same converged energies
+    # (the counts vary by a few products between runs: the order of the FP32 gradient sums)
+    assert n_mlp < n_diag, (n_mlp, n_diag)
+
+
+def test_training_after_the_sample_ring_wraps(P):
+    # enough harvested iterates to fill the sample ring and wrap around: training must only
+    # draw from written samples (loss and parameters finite)
+    prob = make_problem("sd", 4, 4, 0, seed=1)
+    d = P.DMRG(prob)
+    d.build_blocks(initial_mps(prob, 256, 5))
+    d.mlp_harvest(True, 2048)
+    d.sweep(256)
+    d.sweep(256)
+    d.mlp_harvest(False)
+    d.mlp_reset(3)
+    loss, ns = d.mlp_train(epochs=1, batch=1024, lr=1e-3, seed=3)
+    assert ns > 200000
+    assert np.isfinite(loss)
+    assert np.all(np.isfinite(d.mlp_params()))
