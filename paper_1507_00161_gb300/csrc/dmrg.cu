@@ -132,6 +132,16 @@ struct Prefetch {
   uint64_t gen = 0;
   EnlPlan plan;
   std::exception_ptr err;
+  // device part issued ahead on a stream of its own (dev_ready: out and lay hold the result,
+  // complete once `done` has fired; the small tables live until then)
+  bool dev_ready = false;
+  Layout lay;
+  OpSet out;
+  DevBuf<LayDev> t_lay;
+  DevBuf<EnlBlock> t_blocks;
+  DevBuf<int8_t> t_par;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
 };
 
 struct Super {
@@ -239,6 +249,12 @@ struct dmrg_ctx {
   bool rq_pending = false;
   ~dmrg_ctx() {
     if (pf.th.joinable()) pf.th.join();
+    if (pf.st) {
+      cudaStreamSynchronize(pf.st);
+      cudaStreamDestroy(pf.st);
+    }
+    if (pf.ready) cudaEventDestroy(pf.ready);
+    if (pf.done) cudaEventDestroy(pf.done);
     if (rq_stream) {
       cudaStreamSynchronize(rq_stream);
       cudaStreamDestroy(rq_stream);
@@ -630,9 +646,11 @@ static void plan_enlarge(const Ctx& c, const OpSet& blk, int s, bool left, EnlPl
   elap(14);
 }
 
-// Device part: the arena, the tables, the kernel (context stream, waited for).
+// Device part: the arena, the tables, the kernel.  Without `ahead`: on the context stream,
+// waited for.  With `ahead`: on the prefetch stream after the context stream's work so far,
+// not waited for; the tables are kept in `ahead` until the result is used.
 static void exec_enlarge(Ctx& c, OpSet& blk, int s, bool left, EnlPlan& P, Layout& lay,
-                         OpSet& out) {
+                         OpSet& out, Prefetch* ahead = nullptr) {
   double te = wall();
   ensure_dev_index(c, blk);
   c.t_detail[9] += wall() - te;
@@ -640,23 +658,41 @@ static void exec_enlarge(Ctx& c, OpSet& blk, int s, bool left, EnlPlan& P, Layou
   lay = std::move(P.lay);
   out = std::move(P.out);
   out.data.alloc(out.n_elems + 4);
+  cudaStream_t st = c.stream;
+  if (ahead) {
+    if (!ahead->st) {
+      DMRG_CUDA(cudaStreamCreateWithFlags(&ahead->st, cudaStreamNonBlocking));
+      DMRG_CUDA(cudaEventCreateWithFlags(&ahead->ready, cudaEventDisableTiming));
+      DMRG_CUDA(cudaEventCreateWithFlags(&ahead->done, cudaEventDisableTiming));
+    }
+    // pool memory handed out above may still be in use by earlier work on the context stream
+    DMRG_CUDA(cudaEventRecord(ahead->ready, c.stream));
+    DMRG_CUDA(cudaStreamWaitEvent(ahead->st, ahead->ready, 0));
+    st = ahead->st;
+  }
   const int nparts = int(P.part.size());
   DevBuf<LayDev> dlay;
   DevBuf<EnlBlock> deb;
-  dlay.upload(P.ld, c.stream);
+  dlay.upload(P.ld, st);
   deb.alloc(std::max<int64_t>(P.pbase[nparts], 1));
   for (int t = 0; t < nparts; ++t)
     if (!P.part[t].empty())
       DMRG_CUDA(cudaMemcpyAsync(deb.p + P.pbase[t], P.part[t].data(),
-                                sizeof(EnlBlock) * P.part[t].size(), cudaMemcpyHostToDevice,
-                                c.stream));
+                                sizeof(EnlBlock) * P.part[t].size(), cudaMemcpyHostToDevice, st));
   const int64_t n_eb = P.pbase[nparts];
   const auto& spar = left ? c.mpo.parity[s] : c.mpo.parity[s + 1];
   DevBuf<int8_t> dpar;
-  dpar.upload(spar, c.stream);
+  dpar.upload(spar, st);
   enlarge_blocks(deb.p, n_eb, se.dptr.p, se.de.p, blk.d_by_in.p, blk.sec.size(), blk.d_boff.p,
                  blk.d_dim.p, blk.d_npart.p, dpar.p, dlay.p, left ? 1 : 0, blk.data.p,
-                 out.data.p, c.stream);
+                 out.data.p, st);
+  if (ahead) {
+    DMRG_CUDA(cudaEventRecord(ahead->done, st));
+    ahead->t_lay = std::move(dlay);
+    ahead->t_blocks = std::move(deb);
+    ahead->t_par = std::move(dpar);
+    return;
+  }
   te = wall();
   sync(c);   // the small tables above are released
   c.t_detail[7] += wall() - te;
@@ -667,8 +703,28 @@ static void wait_prefetch(Ctx& c) {
 }
 
 // a finished plan for (blk, s, left) if one was prefetched
+// the enlarged set issued ahead for (blk, s, left), made visible to the context stream
+static bool take_prefetch_device(Ctx& c, uint64_t gen, int s, bool left, Layout& lay,
+                                 OpSet& out) {
+  if (!c.pf.dev_ready || c.pf.s != s || c.pf.left != left) return false;
+  c.pf.dev_ready = false;
+  c.pf.active = false;
+  DMRG_CUDA(cudaStreamWaitEvent(c.stream, c.pf.done, 0));
+  // the tables go back to the pool once the context stream is past the kernel
+  c.pf.t_lay.release();
+  c.pf.t_blocks.release();
+  c.pf.t_par.release();
+  if (c.pf.gen != gen) {   // stale (cannot happen within a sweep): drop it
+    c.pf.out = OpSet();
+    return false;
+  }
+  lay = std::move(c.pf.lay);
+  out = std::move(c.pf.out);
+  return true;
+}
+
 static bool take_prefetch(Ctx& c, uint64_t gen, int s, bool left, EnlPlan& P) {
-  if (!c.pf.active || c.pf.s != s || c.pf.left != left) return false;   // kept for later
+  if (!c.pf.active || c.pf.dev_ready || c.pf.s != s || c.pf.left != left) return false;
   wait_prefetch(c);
   c.pf.active = false;
   const bool hit = !c.pf.err && c.pf.s == s && c.pf.left == left && c.pf.gen == gen;
@@ -681,6 +737,14 @@ static bool take_prefetch(Ctx& c, uint64_t gen, int s, bool left, EnlPlan& P) {
 // plan the enlargement of blk by site s on a host thread (gen: blk's generation)
 static void start_prefetch(Ctx& c, const OpSet& blk, uint64_t gen, int s, bool left) {
   wait_prefetch(c);
+  if (c.pf.dev_ready) {   // an unused result: drop it once its kernel is done
+    DMRG_CUDA(cudaStreamSynchronize(c.pf.st));
+    c.pf.dev_ready = false;
+    c.pf.out = OpSet();
+    c.pf.t_lay.release();
+    c.pf.t_blocks.release();
+    c.pf.t_par.release();
+  }
   ensure_site_entries(c, s, left);   // main thread: may upload
   c.pf.active = true;
   c.pf.s = s;
@@ -700,10 +764,24 @@ static void start_prefetch(Ctx& c, const OpSet& blk, uint64_t gen, int s, bool l
   });
 }
 
+// once its plan is made, issue the prefetched enlargement on the prefetch stream (called
+// while the context stream is nearly idle: after Davidson)
+static void issue_prefetch_device(Ctx& c, OpSet& blk) {
+  if (!c.pf.active || c.pf.dev_ready) return;
+  wait_prefetch(c);
+  if (c.pf.err) return;
+  c.pf.active = false;   // the plan is consumed; restored once the launch is issued
+  exec_enlarge(c, blk, c.pf.s, c.pf.left, c.pf.plan, c.pf.lay, c.pf.out, &c.pf);
+  c.pf.plan = EnlPlan();
+  c.pf.active = true;
+  c.pf.dev_ready = true;
+}
+
 // operators of the enlarged space; blk_gen identifies blk for a prefetched plan (0: none)
 static void enlarge(Ctx& c, OpSet& blk, int s, bool left, Layout& lay, OpSet& out,
                     uint64_t blk_gen = 0) {
   PhaseTimer tm(c.t_enlarge);
+  if (blk_gen && take_prefetch_device(c, blk_gen, s, left, lay, out)) return;
   const double th0 = wall();
   EnlPlan P;
   if (!(blk_gen && take_prefetch(c, blk_gen, s, left, P))) {
@@ -1839,7 +1917,10 @@ static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
 // ---------------------------------------------------------------------------------------
 static void build_blocks(Ctx& c, const dmrg_mps_init* init) {
   wait_prefetch(c);
+  if (c.pf.st) DMRG_CUDA(cudaStreamSynchronize(c.pf.st));
   c.pf.active = false;
+  c.pf.dev_ready = false;
+  c.pf.out = OpSet();
   const int N = c.N;
   cudaStream_t s = c.stream;
   c.left.clear();
@@ -1938,6 +2019,8 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   predict(c, sb, p, dir, c.psi_guess.p);
   c.psi.alloc(std::max<int64_t>(sb.size, 1));
   DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p, true);
+  if (dir == 0 && p + 2 <= c.N - 2 && c.right[p + 2].valid) issue_prefetch_device(c, c.right[p + 2].ops);
+  else if (dir == 1 && p - 2 >= 0 && c.left[p - 2].valid) issue_prefetch_device(c, c.left[p - 2].ops);
   const double flops = sb.flops, bytes = sb.bytes;
   c.psi_valid = true;
   c.psi_p = p;
