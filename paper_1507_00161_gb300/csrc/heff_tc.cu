@@ -52,12 +52,17 @@ __device__ __forceinline__ void stage_async(float* dst, const float* src, int el
   const int nv = (elems + 3) >> 2;
   for (int v = lane; v < nv; v += 32) cp_async16(dst + 4 * v, src + 4 * v);
 }
-// rows x cols of a row-major source (ld) into dst with leading dimension cols
-__device__ __forceinline__ void stage_sync(float* dst, const float* src, int rows, int cols, int ld,
-                                           int lane) {
+// rows x cols of a row-major source (ld) into dst with leading dimension cols, as 4-byte
+// asynchronous copies (rows of a chunk need not start on 16-byte boundaries)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void stage_chunk(float* dst, const float* src, int rows, int cols,
+                                            int ld, int lane) {
   for (int e = lane; e < rows * cols; e += 32) {
     const int r = e / cols, c = e - r * cols;
-    dst[e] = src[(int64_t)r * ld + c];
+    cp_async4(dst + e, src + (int64_t)r * ld + c);
   }
 }
 
@@ -233,12 +238,15 @@ __global__ void __launch_bounds__(kW * 32, 3)
     if (inflight == 0) {
       // large term: 32-wide chunks staged synchronously into the (empty) ring
       ++issued;
+      // (asynchronous copies: the L chunk is in flight while the psi and R chunks load)
       float* const Pc = ring;                 // psi chunk (kc x rc)
       float* const Rc = ring + kT * kT;       // R chunk (n x rc)
-      float* const Lc = ring;                 // L chunk (m x kc), once psi and R are used
+      float* const Lc = ring + 2 * kT * kT;   // L chunk (m x kc)
       for (int k0 = 0; k0 < dLi; k0 += kT) {
         const int kc = min(kT, dLi - k0);
         const int MT1 = (kc + 15) >> 4;
+        stage_chunk(Lc, L + it.loff + (int64_t)t.r0 * dLi + k0, m, kc, dLi, lane);
+        cp_commit();
         float cX[2][4][4];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
@@ -248,14 +256,15 @@ __global__ void __launch_bounds__(kW * 32, 3)
             for (int e = 0; e < 4; ++e) cX[a][b][e] = 0.f;
         for (int r0 = 0; r0 < dRi; r0 += kT) {
           const int rc = min(kT, dRi - r0);
-          stage_sync(Pc, X + it.xoff + (int64_t)k0 * dRi + r0, kc, rc, dRi, lane);
-          stage_sync(Rc, R + it.roff + (int64_t)t.c0 * dRi + r0, n, rc, dRi, lane);
+          stage_chunk(Pc, X + it.xoff + (int64_t)k0 * dRi + r0, kc, rc, dRi, lane);
+          stage_chunk(Rc, R + it.roff + (int64_t)t.c0 * dRi + r0, n, rc, dRi, lane);
+          cp_commit();
+          cp_wait<0>();
           __syncwarp();
           stage1(cX, Pc, rc, kc, Rc, rc, n, rc, MT1, NT, gid, tig);
           __syncwarp();
         }
         store_x(Xs, cX, it.sign, MT1, NT, gid, tig);
-        stage_sync(Lc, L + it.loff + (int64_t)t.r0 * dLi + k0, m, kc, dLi, lane);
         __syncwarp();
         stage2(acc, Lc, kc, m, kc, Xs, MT2, NT, gid, tig);
         __syncwarp();
