@@ -57,6 +57,23 @@ __device__ __forceinline__ int term_elems(int m, int n, int dLi, int dRi) {
   return round_vec<T>(m * dLi) + round_vec<T>(n * dRi) + round_vec<T>(dLi * dRi);
 }
 
+// rows x cols of a row-major source (ld) into dst (leading dimension cols), one
+// asynchronous copy per element (chunk rows need not start on 16-byte boundaries)
+template <class T>
+__device__ __forceinline__ void stage_chunk(T* dst, const T* src, int rows, int cols, int ld,
+                                            int lane) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+  for (int e = lane; e < rows * cols; e += 32) {
+    const int r = e / cols, cc = e - r * cols;
+    const unsigned sm = static_cast<unsigned>(__cvta_generic_to_shared(dst + e));
+    const T* g = src + (int64_t)r * ld + cc;
+    if (sizeof(T) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sm), "l"(g) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sm), "l"(g) : "memory");
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void stage(T* dst, const T* src, int elems, int lane) {
   const int nv = (elems * int(sizeof(T)) + 15) / 16;
@@ -138,27 +155,44 @@ __global__ void __launch_bounds__(kW * 32, sizeof(T) == 4 ? 4 : 2)
     const T sg = T(it.sign);
     const int dLi = it.dLi, dRi = it.dRi;
     if (inflight == 0) {
-      // large term: chunked, straight from global memory
+      // large term: chunks staged into the (empty) ring by asynchronous copies; X rows
+      // accumulate in shared memory over the chunks of the psi columns (same order of
+      // summation as a single pass)
       ++issued;
-      for (int k0 = 0; k0 < dLi; k0 += kT) {
-        const int kc = min(kT, dLi - k0);
-        if (act) {
-          const T* rr = R + it.roff + (int64_t)(t.c0 + c) * dRi;
-          for (int i = g; i < kc; i += G) {
-            const T* pr = X + it.xoff + (int64_t)(k0 + i) * dRi;
-            T s = T(0);
-            for (int r = 0; r < dRi; ++r) s = fma(pr[r], rr[r], s);
-            Xs[i * (kT + 1) + c] = s;
+      constexpr int KC = kRing / (3 * kT) < kT ? kRing / (3 * kT) : kT;   // rows per chunk
+      T* const Pc = ring;              // psi chunk (kc x rc), then the L chunk (m x kc)
+      T* const Rc = ring + KC * kT;    // R chunk (n x rc)
+      for (int k0 = 0; k0 < dLi; k0 += KC) {
+        const int kc = min(KC, dLi - k0);
+        for (int r0 = 0; r0 < dRi; r0 += kT) {
+          const int rc = min(kT, dRi - r0);
+          stage_chunk(Pc, X + it.xoff + (int64_t)k0 * dRi + r0, kc, rc, dRi, lane);
+          stage_chunk(Rc, R + it.roff + (int64_t)t.c0 * dRi + r0, n, rc, dRi, lane);
+          cp_commit();
+          cp_wait<0>();
+          __syncwarp();
+          if (act) {
+            const T* rr = Rc + c * rc;
+            for (int i = g; i < kc; i += G) {
+              const T* pr = Pc + i * rc;
+              T s = r0 ? Xs[i * (kT + 1) + c] : T(0);
+              for (int r = 0; r < rc; ++r) s = fma(pr[r], rr[r], s);
+              Xs[i * (kT + 1) + c] = s;
+            }
           }
+          __syncwarp();
         }
+        stage_chunk(Pc, L + it.loff + (int64_t)t.r0 * dLi + k0, m, kc, dLi, lane);
+        cp_commit();
+        cp_wait<0>();
         __syncwarp();
         if (act) {
+          const T* lr = Pc + g * kc;
           for (int k = 0; k < kc; ++k) {
             const T xv = sg * Xs[k * (kT + 1) + c];
-            const T* lc = L + it.loff + (int64_t)(t.r0 + g) * dLi + k0 + k;
 #pragma unroll
             for (int q = 0; q < kT; ++q)
-              if (q < rows_mine) acc[q] = fma(lc[(int64_t)q * G * dLi], xv, acc[q]);
+              if (q < rows_mine) acc[q] = fma(lr[q * G * kc + k], xv, acc[q]);
           }
         }
         __syncwarp();
