@@ -246,7 +246,10 @@ struct dmrg_ctx {
   cudaStream_t rq_stream = nullptr;
   cudaEvent_t rq_in = nullptr, rq_out = nullptr;
   dmrg::DevBuf<double> rq_part;
-  bool rq_pending = false;
+  bool rq_pending = false, rq_todo = false;
+  dmrg::Super* rq_sb = nullptr;
+  int64_t rq_n = 0;
+  double* rq_sc = nullptr;
   ~dmrg_ctx() {
     if (pf.th.joinable()) pf.th.join();
     if (pf.st) {
@@ -1536,13 +1539,11 @@ static void dav_finish(Ctx& c, DavRun& R) {
     c.rq_part.alloc(64 * 300);
     c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad64.alloc(sb.pad_size);
-    DMRG_CUDA(cudaEventRecord(c.rq_in, c.stream));
-    DMRG_CUDA(cudaStreamWaitEvent(c.rq_stream, c.rq_in, 0));
-    heff64(c, sb, c.x.p, c.Ax.p, c.rq_stream);
-    dot(c.x.p, c.Ax.p, n, P.sc + 5, c.rq_part.p, c.rq_stream);
-    DMRG_CUDA(cudaMemcpyAsync(c.h_words + 32, P.sc + 5, sizeof(double), cudaMemcpyDeviceToHost,
-                              c.rq_stream));
-    DMRG_CUDA(cudaEventRecord(c.rq_out, c.rq_stream));
+    DMRG_CUDA(cudaEventRecord(c.rq_in, c.stream));   // the normalized vector is ready
+    c.rq_sb = &sb;
+    c.rq_n = n;
+    c.rq_sc = P.sc + 5;
+    c.rq_todo = true;   // launched by launch_rq (the truncation first gets the GPU)
     c.rq_pending = true;
   }
   (void)h;
@@ -1633,8 +1634,22 @@ static void dav_after_product(Ctx& c, DavRun& R) {
   R.py = avec(R.k);
 }
 
+// issue the FP64 Rayleigh quotient prepared by dav_finish (on its own stream, after the
+// vector it needs); the superblock stays alive until the next truncation replaces c.prev
+static void launch_rq(Ctx& c) {
+  if (!c.rq_todo) return;
+  c.rq_todo = false;
+  DMRG_CUDA(cudaStreamWaitEvent(c.rq_stream, c.rq_in, 0));
+  heff64(c, *c.rq_sb, c.x.p, c.Ax.p, c.rq_stream);
+  dot(c.x.p, c.Ax.p, c.rq_n, c.rq_sc, c.rq_part.p, c.rq_stream);
+  DMRG_CUDA(cudaMemcpyAsync(c.h_words + 32, c.rq_sc, sizeof(double), cudaMemcpyDeviceToHost,
+                            c.rq_stream));
+  DMRG_CUDA(cudaEventRecord(c.rq_out, c.rq_stream));
+}
+
 // energy of a finished run: the FP64 Rayleigh quotient of the mixed path once it is done
 static void dav_energy(Ctx& c, DavResult& r) {
+  launch_rq(c);
   if (!c.rq_pending) return;
   const double t0 = wall();
   DMRG_CUDA(cudaEventSynchronize(c.rq_out));
@@ -1697,6 +1712,7 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
   Iso iso;
   TruncResult tr;
   if (total <= M) {
+    launch_rq(c);
     identity_iso(c, lay, iso);
     tr.trunc = 0.0;
     tr.kept = int(total);
@@ -1752,6 +1768,7 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     DMRG_CUDA(cudaMemcpyAsync(kept.data(), dkept.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, s));
     DMRG_CUDA(cudaMemcpyAsync(kwh.data(), kw, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
     sync(c);
+    launch_rq(c);   // the density-matrix decomposition is done: the energy may take the GPU
     iso.lay = lay;
     iso.m.assign(ns, 0);
     iso.uoff.assign(ns, 0);
@@ -1780,6 +1797,10 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
   dst.iso = std::move(iso);
   dst.valid = true;
   dst.gen = ++g_blk_gen;
+  if (c.rq_pending && c.rq_sb != c.sb.get()) {   // a Rayleigh quotient still reads c.prev
+    launch_rq(c);
+    DMRG_CUDA(cudaEventSynchronize(c.rq_out));
+  }
   c.prev = std::move(c.sb);   // layouts of the superblock psi belongs to
   return tr;
 }
