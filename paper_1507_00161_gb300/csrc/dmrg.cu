@@ -247,6 +247,7 @@ struct dmrg_ctx {
   cudaEvent_t rq_in = nullptr, rq_out = nullptr;
   dmrg::DevBuf<double> rq_part;
   bool rq_pending = false, rq_todo = false;
+  double* rq_target = nullptr;   // where a deferred energy goes (sweeps)
   dmrg::Super* rq_sb = nullptr;
   int64_t rq_n = 0;
   double* rq_sc = nullptr;
@@ -1658,6 +1659,18 @@ static void dav_energy(Ctx& c, DavResult& r) {
   c.rq_pending = false;
 }
 
+// a Rayleigh quotient left running by the previous step of a sweep: wait, store the energy
+static void settle_energy(Ctx& c) {
+  if (!c.rq_target) return;
+  launch_rq(c);
+  const double t0 = wall();
+  DMRG_CUDA(cudaEventSynchronize(c.rq_out));
+  c.t_sync += wall() - t0;
+  *c.rq_target = c.h_words[32];
+  c.rq_target = nullptr;
+  c.rq_pending = false;
+}
+
 // defer_energy: leave the Rayleigh quotient of the mixed path running (dav_energy waits)
 static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out,
                           bool defer_energy = false) {
@@ -2027,7 +2040,10 @@ static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
+// late_energy: in a sweep, the mixed path's energy of this step is stored there once the next
+// step has built its superblock (its Rayleigh quotient overlaps that host work)
+static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st,
+                 double* late_energy = nullptr) {
   double t0 = now_s();
   Super& sb = super_at(c, p);
   // the block that the next step of this sweep enlarges on the side this step leaves as
@@ -2039,6 +2055,7 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   c.psi_guess.alloc(std::max<int64_t>(sb.size, 1));
   predict(c, sb, p, dir, c.psi_guess.p);
   c.psi.alloc(std::max<int64_t>(sb.size, 1));
+  settle_energy(c);   // the previous step's energy (its product reads vectors Davidson reuses)
   DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p, true);
   if (dir == 0 && p + 2 <= c.N - 2 && c.right[p + 2].valid) issue_prefetch_device(c, c.right[p + 2].ops);
   else if (dir == 1 && p - 2 >= 0 && c.left[p - 2].valid) issue_prefetch_device(c, c.left[p - 2].ops);
@@ -2046,7 +2063,8 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
   c.psi_valid = true;
   c.psi_p = p;
   TruncResult tr = truncate_renormalize(c, p, dir, M);   // overlaps the Rayleigh quotient
-  dav_energy(c, r);
+  const bool late = late_energy && c.rq_pending;
+  if (!late) dav_energy(c, r);
   if (st) {
     st->p = p;
     st->dir = dir;
@@ -2059,6 +2077,10 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st) {
     st->heff_seconds = r.heff_seconds;
     st->heff_flops = flops;
     st->heff_bytes = bytes;
+  }
+  if (late) {
+    launch_rq(c);
+    c.rq_target = late_energy;
   }
 }
 
@@ -2275,19 +2297,18 @@ extern "C" int dmrg_step(dmrg_ctx* c, int32_t p, int32_t dir, int32_t M, dmrg_st
 extern "C" int dmrg_sweep(dmrg_ctx* c, int32_t M, dmrg_step_stats* steps, double* energy) {
   return guarded(c, [&] {
     DMRG_REQUIRE(c->built, DMRG_EINVAL, "dmrg_build_blocks has not been called");
+    std::vector<dmrg_step_stats> all(2 * size_t(c->N - 3));
     int k = 0;
-    dmrg_step_stats st{};
-    for (int p = 1; p <= c->N - 3; ++p) {
-      step(*c, p, 0, M, &st);
-      if (steps) steps[k] = st;
-      ++k;
+    try {
+      for (int p = 1; p <= c->N - 3; ++p, ++k) step(*c, p, 0, M, &all[k], &all[k].energy);
+      for (int p = c->N - 3; p >= 1; --p, ++k) step(*c, p, 1, M, &all[k], &all[k].energy);
+      settle_energy(*c);
+    } catch (...) {
+      c->rq_target = nullptr;   // the stats are local to this call
+      throw;
     }
-    for (int p = c->N - 3; p >= 1; --p) {
-      step(*c, p, 1, M, &st);
-      if (steps) steps[k] = st;
-      ++k;
-    }
-    if (energy) *energy = st.energy;
+    if (steps) std::copy(all.begin(), all.end(), steps);
+    if (energy && !all.empty()) *energy = all.back().energy;
   });
 }
 
