@@ -95,6 +95,26 @@ __device__ __forceinline__ void mma3(float (&d)[4], const float (&a)[4], const f
   mma(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
 }
 
+// the same for two accumulators sharing a: their MMA chains are interleaved so that each
+// MMA does not wait on the one just issued (same order of the three terms per accumulator)
+__device__ __forceinline__ void mma3_2b(float (&d0)[4], float (&d1)[4], const float (&a)[4],
+                                        const float (&b0)[2], const float (&b1)[2]) {
+  uint32_t ah[4], al[4], bh0[2], bl0[2], bh1[2], bl1[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split(a[i], ah[i], al[i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    split(b0[i], bh0[i], bl0[i]);
+    split(b1[i], bh1[i], bl1[i]);
+  }
+  mma(d0, al[0], al[1], al[2], al[3], bh0[0], bh0[1]);
+  mma(d1, al[0], al[1], al[2], al[3], bh1[0], bh1[1]);
+  mma(d0, ah[0], ah[1], ah[2], ah[3], bl0[0], bl0[1]);
+  mma(d1, ah[0], ah[1], ah[2], ah[3], bl1[0], bl1[1]);
+  mma(d0, ah[0], ah[1], ah[2], ah[3], bh0[0], bh0[1]);
+  mma(d1, ah[0], ah[1], ah[2], ah[3], bh1[0], bh1[1]);
+}
+
 // element (r, c) of a row-major rows x cols matrix, zero outside
 __device__ __forceinline__ float at(const float* M, int ld, int rows, int cols, int r, int c) {
   return (r < rows && c < cols) ? M[r * ld + c] : 0.f;
@@ -108,17 +128,21 @@ __device__ __forceinline__ void stage1(float (&cX)[2][4][4], const float* P, int
   for (int ks = 0; ks < KS; ++ks) {
     const int k0 = ks * 8 + tig, k1 = k0 + 4;
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
+    for (int nt = 0; nt < 4; nt += 2) {   // column tiles in pairs (interleaved chains)
       if (nt >= NT) break;
       const int col = nt * 8 + gid;
       const float b[2] = {at(R, ldr, n, kdim, col, k0), at(R, ldr, n, kdim, col, k1)};
+      const bool two = nt + 1 < NT;
+      const float b1[2] = {two ? at(R, ldr, n, kdim, col + 8, k0) : 0.f,
+                           two ? at(R, ldr, n, kdim, col + 8, k1) : 0.f};
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
         if (mt >= MT) break;
         const int r0 = mt * 16 + gid, r1 = r0 + 8;
         const float a[4] = {at(P, ldp, rows, kdim, r0, k0), at(P, ldp, rows, kdim, r1, k0),
                             at(P, ldp, rows, kdim, r0, k1), at(P, ldp, rows, kdim, r1, k1)};
-        mma3(cX[mt][nt], a, b);
+        if (two) mma3_2b(cX[mt][nt], cX[mt][nt + 1], a, b, b1);
+        else mma3(cX[mt][nt], a, b);
       }
     }
   }
@@ -150,17 +174,20 @@ __device__ __forceinline__ void stage2(float (&acc)[2][4][4], const float* Ls, i
   for (int ks = 0; ks < KS; ++ks) {
     const int k0 = ks * 8 + tig, k1 = k0 + 4;
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
+    for (int nt = 0; nt < 4; nt += 2) {   // column tiles in pairs (interleaved chains)
       if (nt >= NT) break;
       const int col = nt * 8 + gid;
       const float b[2] = {Xs[k0 * kXLD + col], Xs[k1 * kXLD + col]};
+      const bool two = nt + 1 < NT;
+      const float b1[2] = {Xs[k0 * kXLD + col + 8], Xs[k1 * kXLD + col + 8]};
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
         if (mt >= MT) break;
         const int r0 = mt * 16 + gid, r1 = r0 + 8;
         const float a[4] = {at(Ls, ldl, m, kdim, r0, k0), at(Ls, ldl, m, kdim, r1, k0),
                             at(Ls, ldl, m, kdim, r0, k1), at(Ls, ldl, m, kdim, r1, k1)};
-        mma3(acc[mt][nt], a, b);
+        if (two) mma3_2b(acc[mt][nt], acc[mt][nt + 1], a, b, b1);
+        else mma3(acc[mt][nt], a, b);
       }
     }
   }
