@@ -39,7 +39,7 @@ WORKLOAD_NAME = ("pf-shell 40 sites, 8p+8n, M_z=0 (m-scheme dim 1,087,455,228), 
 # DRAM bytes (read + write) per mixed H_eff product of the default workload, from the one-pass
 # ncu capture of the timed steps in profiles/step_kernels_pf8p8n_M4096.md (sum over the
 # product's kernels / products); to be re-taken whenever those kernels change
-HEFF_TRAFFIC_BYTES = 175.2e6
+HEFF_TRAFFIC_BYTES = 175.3e6
 CPU_SAMPLE = dict(space="sd", Np=2, Nn=2, two_Mz=0, seed=1, mps_seed=5, M=64)
 
 
