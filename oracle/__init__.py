@@ -16,5 +16,9 @@ Contents and pins (each checked by a ``-m "not gpu"`` test):
   Jordan-Wigner matrices, at every bond, in both operator modes.
 * ``dmrg``: two-site DMRG.  Pinned by full-M runs reproducing exact diagonalization,
   the variational bound, energies non-increasing in M, Hermiticity of H_eff,
-  H_eff on exact states, and truncation error -> 0 at full M.
+  H_eff on exact states, and truncation error -> 0 at full M.  Its dynamic block state
+  selection is pinned by brute force on singular values of the wave-function blocks,
+  by its reductions to the fixed-M rule, and by the truncation bound along sweeps.
+* ``extrapolate``: least-squares E(M) fits.  Pinned by exact model data, the normal
+  equations, an independent exponent scan and equivariance under shift and scale.
 """

@@ -29,8 +29,13 @@ Readings where the paper is silent (they are the same in the CUDA library):
 * truncation: rho per sector, eigenvalues clipped at 0; if more states than M: sort by
   lambda descending, ties by sector then index; with lambda_M the M-th, keep every state
   with lambda >= max(lambda_M (1 - 1e-10), 1e-14) (never splits a degenerate multiplet);
-  otherwise keep all.  Eigenvector sign: largest |component| positive (lowest index on
-  ties); kept states of a sector in descending lambda;
+  otherwise keep all.  Dynamic block state selection (DBSS, optional): M is the ceiling,
+  m_min the floor (keep all when there are at most min(m_min, M) states), and the count
+  at the cut is the fewest k >= min(m_min, M), k <= min(M, total), whose discarded weight
+  1 - (lambda_1 + ... + lambda_k) (descending, summed in that order) is at most the
+  target, else min(M, total); the same multiplet and 1e-14 rules follow.  Eigenvector
+  sign: largest |component| positive (lowest index on ties); kept states of a sector in
+  descending lambda;
 * initial guess: the uniform vector at the first step, then White's transformation of
   the previous wave function through the new block basis and the stored basis of the
   neighbouring block; the same wave function when a sweep turns around.
@@ -289,8 +294,25 @@ def davidson(apply, diag, x0, tol=1e-8, max_iter=100, max_sub=24):
 # ----------------------------------------------------------------------------------
 # truncation by the reduced density matrix
 # ----------------------------------------------------------------------------------
-def truncate(psi: np.ndarray, lay: Layout, enl: Block, side: str, M: int):
-    """Returns (U per kept sector, kept count per sector, truncation error, eigenvalues)."""
+def dbss_count(w_desc, k_min: int, k_max: int, target: float) -> int:
+    """Dynamic block state selection (method section, DBSS with an a priori truncation
+    error): the fewest states k, k_min <= k <= k_max, whose discarded weight
+    1 - (w_1 + ... + w_k) is at most ``target``; k_max when no k qualifies.  The weights
+    come sorted descending and are summed in that order."""
+    kept = 0.0
+    for k in range(1, k_max + 1):
+        kept += float(w_desc[k - 1])
+        if k >= k_min and 1.0 - kept <= target:
+            return k
+    return k_max
+
+
+def truncate(psi: np.ndarray, lay: Layout, enl: Block, side: str, M: int, m_min: int = 0,
+             trunc_target: float = 0.0):
+    """Returns (U per kept sector, kept count per sector, truncation error, eigenvalues).
+
+    trunc_target > 0 selects dynamically: M is the ceiling, m_min the floor, and the count
+    at the cut is ``dbss_count``; otherwise M states are kept."""
     rho = {}
     for (QL, QR, dL, dR, off) in lay.blocks:
         P = psi[off:off + dL * dR].reshape(dL, dR)
@@ -308,11 +330,16 @@ def truncate(psi: np.ndarray, lay: Layout, enl: Block, side: str, M: int):
         evals[Q], evecs[Q] = w, V
     allv = [(-evals[Q][i], Q, i) for Q in enl.sectors for i in range(enl.dims[Q])]
     total = len(allv)
-    if total <= M:
+    dbss = trunc_target > 0.0
+    floor = min(m_min, M) if dbss else M
+    if total <= floor:
         keep = {Q: enl.dims[Q] for Q in enl.sectors}
     else:
         allv.sort()
-        lamM = -allv[M - 1][0]
+        k = min(M, total)
+        if dbss:
+            k = dbss_count([-v[0] for v in allv], floor, k, trunc_target)
+        lamM = -allv[k - 1][0]
         thr = max(lamM * (1.0 - 1e-10), 1e-14)
         keep = {Q: int(np.sum(evals[Q] >= thr)) for Q in enl.sectors}
     U = {}
@@ -343,7 +370,9 @@ class StepResult:
 
 
 class OracleDMRG:
-    def __init__(self, prob, init_mps, tol=1e-8, max_iter=100, max_sub=24):
+    def __init__(self, prob, init_mps, tol=1e-8, max_iter=100, max_sub=24, m_min=0,
+                 trunc_target=0.0):
+        self.m_min, self.trunc_target = m_min, trunc_target   # DBSS (trunc_target > 0)
         self.ch = ch = ChainHamiltonian(prob)
         self.mpo = mpo = MPO(ch)
         self.N = N = ch.N
@@ -441,11 +470,11 @@ class OracleDMRG:
         theta, x, nprod, rn = davidson(sb.apply, diag, x0, self.tol, self.max_iter,
                                        self.max_sub)
         if direction == "L":
-            U, keep, tr, _ = truncate(x, sb.layout, sb.L, "L", M)
+            U, keep, tr, _ = truncate(x, sb.layout, sb.L, "L", M, self.m_min, self.trunc_target)
             self.UL[p] = U
             self.left[p] = project(sb.L, U)
         else:
-            U, keep, tr, _ = truncate(x, sb.layout, sb.R, "R", M)
+            U, keep, tr, _ = truncate(x, sb.layout, sb.R, "R", M, self.m_min, self.trunc_target)
             self.UR[p] = U
             self.right[p] = project(sb.R, U)
         self.psi, self.psi_layout, self.psi_at = x, sb.layout, (p, direction)

@@ -130,3 +130,104 @@ def test_heff_equals_projected_hamiltonian(p_at):
     th, x, _, _ = davidson(sb.apply, sb.diagonal(), np.ones(n), tol=1e-10)
     assert abs(th - np.linalg.eigvalsh(He)[0]) < 1e-10
     assert np.allclose(sb.diagonal(), np.diag(He), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# dynamic block state selection (DBSS): kept count set by an a priori truncation error
+# ---------------------------------------------------------------------------------------
+def _psi_at(p_at=4):
+    from oracle.dmrg import davidson
+    p = make_problem("p", 2, 2, 0, seed=12)
+    d = OracleDMRG(p, initial_mps(p, 6, 5))
+    d.sweep(6)
+    for q in range(1, p_at):
+        d.run_step(q, "L", 6)
+    sb = d.superblock(p_at)
+    _, x, _, _ = davidson(sb.apply, sb.diagonal(), np.ones(sb.layout.size), tol=1e-10)
+    return sb, x
+
+
+def _schmidt_weights(sb, x):
+    """Weights of the enlarged-left states from the singular values of the wave-function
+    blocks (one block per left sector), zero-padded to each sector's dimension."""
+    w = []
+    for (QL, QR, dL, dR, off) in sb.layout.blocks:
+        s = np.linalg.svd(x[off:off + dL * dR].reshape(dL, dR), compute_uv=False)
+        w.extend(s ** 2)
+    n_zero = sum(sb.L.dims.values()) - len(w)
+    return np.sort(np.concatenate([w, np.zeros(n_zero)]))[::-1]
+
+
+@pytest.mark.parametrize("target", [3e-2, 1e-3, 1e-5])
+def test_dbss_keeps_the_fewest_states_within_the_target(target):
+    from oracle.dmrg import truncate
+    sb, x = _psi_at()
+    w = _schmidt_weights(sb, x)
+    D = len(w)
+    for m_min, M in ((1, D), (3, D), (2, 9)):
+        # brute force on the definition: discarded weight = the tail sum of the weights
+        ok = [k for k in range(min(m_min, M), min(M, D) + 1) if np.sum(w[k:]) <= target]
+        k_ref = ok[0] if ok else min(M, D)
+        assert w[k_ref - 1] > 1e-10 and w[k_ref - 1] - w[k_ref] > 1e-12   # no tie at the cut
+        _, keep, tr, _ = truncate(x, sb.layout, sb.L, "L", M, m_min, target)
+        assert sum(keep.values()) == k_ref, (m_min, M, target)
+        assert abs(tr - np.sum(w[k_ref:])) < 1e-12
+        if k_ref < min(M, D):
+            assert tr <= target + 1e-15
+        if k_ref > min(m_min, M):
+            assert np.sum(w[k_ref - 1:]) > target    # one state fewer misses the target
+
+
+def test_dbss_special_cases():
+    from oracle.dmrg import truncate
+    sb, x = _psi_at()
+    D = sum(sb.L.dims.values())
+    U0, keep0, tr0, _ = truncate(x, sb.layout, sb.L, "L", 7)
+    # floor = ceiling: the fixed-M selection
+    U1, keep1, tr1, _ = truncate(x, sb.layout, sb.L, "L", 7, 7, 0.5)
+    assert keep1 == keep0 and tr1 == tr0
+    assert all(np.array_equal(U0[Q], U1[Q]) for Q in U0)
+    # a target every count meets: the floor
+    _, keep2, _, _ = truncate(x, sb.layout, sb.L, "L", 7, 4, 0.999)
+    assert sum(keep2.values()) == 4
+    # a target no count meets below the ceiling: the ceiling
+    _, keep3, _, _ = truncate(x, sb.layout, sb.L, "L", 7, 2, 1e-300)
+    assert keep3 == keep0
+    # no more states than the floor: everything is kept
+    _, keep4, tr4, _ = truncate(x, sb.layout, sb.L, "L", D + 5, D, 1e-3)
+    assert keep4 == dict(sb.L.dims) and tr4 < 1e-13
+
+
+def test_dbss_sweeps_bound_the_truncation_and_reach_exact():
+    """sd shell 2p+2n (m-scheme dimension 640).  From a random start, each DBSS truncation
+    below the ceiling discards at most the target and the energies stay variational.  From
+    the exact state (one sweep with complete bases), a tight target keeps the full CI
+    energy with far fewer states (it drops only the zero weights), and a looser one gives
+    an error that shrinks with the target."""
+    p = make_problem("sd", 2, 2, 0, seed=1)
+    e0 = ed_lowest(p)[0]
+    loose = OracleDMRG(p, initial_mps(p, 8, 5), m_min=16, trunc_target=1e-3)
+    for _ in range(2):
+        res = loose.sweep(64)
+        for r in res:
+            assert r.energy >= e0 - 1e-10
+            if sum(r.kept.values()) < 64:
+                assert r.trunc_err <= 1e-3 + 1e-15
+    kept = [sum(r.kept.values()) for r in res]
+    assert 16 < max(kept) < 64                 # the target, not the ceiling, set the count
+    d = OracleDMRG(p, initial_mps(p, 8, 5))
+    full = d.sweep(400)
+    assert abs(full[-1].energy - e0) < 1e-10
+    n_full = sum(sum(r.kept.values()) for r in full)
+    errs = []
+    for target in (1e-10, 1e-5, 1e-3):        # tightest first: each starts near exact
+        d.m_min, d.trunc_target = 4, target
+        res = d.sweep(400)
+        for r in res:
+            assert r.energy >= e0 - 1e-10
+            assert r.trunc_err <= target + 1e-15
+        errs.append(res[-1].energy - e0)
+        n_dbss = sum(sum(r.kept.values()) for r in res)
+        assert n_dbss < 0.5 * n_full
+    assert abs(errs[0]) < 1e-9
+    assert 1e-8 < errs[1] < 1e-3 and errs[2] > errs[1]
