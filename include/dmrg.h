@@ -202,6 +202,39 @@ int dmrg_step(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t M, dmrg_step_stats*
  * forth").  steps: optional array of 2(N-3) records.  energy: energy of the last step. */
 int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy);
 
+/* Dynamic block state selection (DBSS): the number of kept block states is set by the
+ * truncation error instead of being fixed ("M_max determined by the truncation error
+ * delta eps_TR" of the method section; the paper's runs use M_min = 256 and delta eps_TR =
+ * 1e-3 ... 1e-6).  Once set, the M argument of dmrg_truncate_renormalize, dmrg_step,
+ * dmrg_sweep and dmrg_batch_sweep is the ceiling M_max, and each truncation keeps
+ *   - every state when the enlarged block has at most min(M_min, M_max) states;
+ *   - otherwise the k largest weights (then the whole degenerate multiplet at the cut, as
+ *     with a fixed M), k = the smallest count in [min(M_min, M_max), min(M_max, D)] whose
+ *     discarded weight 1 - (lambda_1 + ... + lambda_k), summed in descending order in
+ *     FP64, is at most trunc_target; k = min(M_max, D) if no count reaches it
+ *     (D = dimension of the enlarged block).
+ * trunc_target <= 0 switches back to a fixed M (the default).  DMRG_EINVAL if
+ * trunc_target >= 1 or is NaN, or M_min < 1 with a positive target. */
+int dmrg_set_dbss(dmrg_ctx* ctx, int32_t M_min, double trunc_target);
+
+/* Extrapolation of energies in the number of kept block states (host code, no context,
+ * no device work).  Points (M[i], E[i]), i < n, are fitted by ordinary least squares:
+ *   DMRG_FIT_POWER:     E(M) = E_inf + X1 M^X2, the truncation-free estimate of the
+ *                       method description; coef = {E_inf, X1, X2}, X2 sought in
+ *                       [-8, -1e-4];
+ *   DMRG_FIT_QUADRATIC: E = c0 + c1 / M + c2 / M^2, the second-order polynomial fit
+ *                       that gives the upper bound in the 64Ge results (the paper does
+ *                       not name the variable; 1/M here); coef = {c0, c1, c2}, c0 is the
+ *                       estimate at M -> infinity.
+ * rms = sqrt(mean squared residual).  coef: host array of 3; M, E: host arrays of n.
+ * DMRG_EINVAL for fewer than three distinct M, M <= 0, a non-finite value, a NULL
+ * pointer or an unknown kind; DMRG_ENOCONV when the best X2 lies on an end of its range
+ * (the energies do not approach a limit as a power of M).  Thread-safe. */
+#define DMRG_FIT_POWER 0
+#define DMRG_FIT_QUADRATIC 1
+int dmrg_extrapolate(int32_t kind, int32_t n, const double* M, const double* E, double* coef,
+                     double* rms);
+
 /* Sectors and dimensions of a stored block basis: side 0 = left block of bond b,
  * side 1 = right block of bond b.  NULL arrays query n. */
 int dmrg_block_sectors(dmrg_ctx* ctx, int32_t side, int32_t b, int32_t* n, int32_t* qn,

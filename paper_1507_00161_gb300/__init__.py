@@ -25,11 +25,11 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
-            "dmrg_set_options", "dmrg_get_counters", "dmrg_heff_cost",
+            "dmrg_set_options", "dmrg_set_dbss", "dmrg_get_counters", "dmrg_heff_cost",
             "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
             "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params",
             "dmrg_batch_create", "dmrg_batch_destroy", "dmrg_batch_last_error",
-            "dmrg_batch_sweep"]
+            "dmrg_batch_sweep", "dmrg_extrapolate"]
 PRECOND_DIAG = 0
 PRECOND_MLP = 1
 
@@ -127,12 +127,14 @@ def load_library(path: str = LIB_PATH):
         "dmrg_block_sectors": [P, i32, i32, P, P, P],
         "dmrg_heff_cost": [P, i32, P, P, P],
         "dmrg_set_options": [P, ctypes.POINTER(Options)],
+        "dmrg_set_dbss": [P, i32, dbl],
         "dmrg_mlp_reset": [P, ctypes.c_uint64],
         "dmrg_mlp_harvest": [P, i32, i32],
         "dmrg_mlp_train": [P, i32, i32, dbl, ctypes.c_uint64, P, P],
         "dmrg_mlp_params": [P, i32, P, i64],
         "dmrg_mlp_loss_grad": [P, i32, P, P, P, i64, P, P],
         "dmrg_get_counters": [P, ctypes.POINTER(Counters)],
+        "dmrg_extrapolate": [i32, i32, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -165,6 +167,30 @@ def _ptr(x):
 
 def _np_ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None and a.size else None
+
+
+FIT_POWER = 0
+FIT_QUADRATIC = 1
+
+
+def extrapolate(M, E, kind=FIT_POWER):
+    """Least-squares fit of energies E at kept-state counts M (host code in the library):
+    FIT_POWER -> (E_inf, X1, X2, rms) of E = E_inf + X1 M^X2; FIT_QUADRATIC ->
+    (c0, c1, c2, rms) of E = c0 + c1/M + c2/M^2."""
+    lib = load_library()
+    m = np.ascontiguousarray(M, dtype=np.float64)
+    e = np.ascontiguousarray(E, dtype=np.float64)
+    if m.shape != e.shape or m.ndim != 1:
+        raise ValueError("M and E must be 1-D arrays of equal length")
+    coef = np.zeros(3)
+    rms = ctypes.c_double()
+    rc = lib.dmrg_extrapolate(int(kind), int(m.shape[0]), _np_ptr(m), _np_ptr(e),
+                              _np_ptr(coef), ctypes.byref(rms))
+    if rc != DMRG_OK:
+        why = {DMRG_EINVAL: "invalid points or kind",
+               DMRG_ENOCONV: "no power-law minimum inside the exponent range"}
+        raise DmrgError(rc, why.get(rc, "fit failed"))
+    return float(coef[0]), float(coef[1]), float(coef[2]), rms.value
 
 
 class DMRG:
@@ -209,6 +235,12 @@ class DMRG:
                     stream=None, precond=PRECOND_DIAG):
         opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream, precond)
         self._check(self.lib.dmrg_set_options(self.h, ctypes.byref(opt)))
+
+    def set_dbss(self, m_min, trunc_target):
+        """Dynamic block state selection: M passed to the truncating calls becomes the
+        ceiling, m_min the floor, and each truncation keeps the fewest states whose
+        discarded weight is at most trunc_target (<= 0: back to a fixed M)."""
+        self._check(self.lib.dmrg_set_dbss(self.h, int(m_min), float(trunc_target)))
 
     def counters(self):
         c = Counters()

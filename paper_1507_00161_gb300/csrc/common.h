@@ -358,9 +358,11 @@ void batched_eigh2(const int64_t* d_off, const int64_t* d_woff, const int32_t* d
                    cudaStream_t s);
 void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w, double* d_Y,
                 cudaStream_t s);
-// global selection: k-th largest of w[0..n) (ties irrelevant for the value), result in out[0]
-void kth_largest(const double* w, int64_t n, int64_t k, double* d_scratch, double* out,
-                 cudaStream_t s);
+// global selection: k-th largest of w[0..n) (ties irrelevant for the value) in out[0] and k
+// in out[1]; k = kmax, or with target > 0 the smallest k in [kmin, kmax] whose discarded
+// weight 1 - (sum of the k largest) is at most target (kmax if none)
+void kth_largest(const double* w, int64_t n, int64_t kmax, int64_t kmin, double target,
+                 double* d_scratch, double* out, cudaStream_t s);
 // kept[s] = number of w >= max(lambda_M (1 - 1e-10), 1e-14) in sector s (w descending)
 void count_kept(const int64_t* d_woff, const int32_t* d_dim, int nsec, const double* w,
                 const double* d_lamM, int32_t* d_kept, double* d_kept_weight, cudaStream_t s);

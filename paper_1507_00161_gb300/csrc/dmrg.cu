@@ -199,6 +199,8 @@ struct dmrg_ctx {
   dmrg::Chain chain;
   dmrg::MPO mpo;
   dmrg_options opt{};
+  int dbss_min = 0;          // dynamic block state selection: M_min (0 = fixed M)
+  double dbss_target = 0.0;  // and the discarded-weight target
   cudaStream_t stream = nullptr;
   int N = 0;
   std::vector<std::set<std::tuple<int, int, int>>> reach_left, reach_right;
@@ -1722,9 +1724,12 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     sq += int64_t(lay.sec.d[i]) * lay.sec.d[i];
     total += lay.sec.d[i];
   }
+  // dynamic block state selection: M is the ceiling, dbss_min the floor
+  const bool dbss = c.dbss_target > 0.0;
+  const int floor_m = dbss ? std::min(c.dbss_min, M) : M;
   Iso iso;
   TruncResult tr;
-  if (total <= M) {
+  if (total <= floor_m) {
     launch_rq(c);
     identity_iso(c, lay, iso);
     tr.trunc = 0.0;
@@ -1773,7 +1778,8 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     batched_eigh2(droff.p, dwoff.p, ddim.p, ns, c.rho.p, c.eV.p, c.eVs.p, c.ew.p, 1, 1, s);
     double* lamM = c.sel.p + np2;
     double* kw = lamM + 8;
-    kth_largest(c.ew.p, total, M, c.sel.p, lamM, s);
+    kth_largest(c.ew.p, total, std::min<int64_t>(M, total), floor_m, dbss ? c.dbss_target : 0.0,
+                c.sel.p, lamM, s);
     dkept.alloc(ns);
     count_kept(dwoff.p, ddim.p, ns, c.ew.p, lamM, dkept.p, kw, s);
     std::vector<int32_t> kept(ns);
@@ -2284,6 +2290,15 @@ extern "C" int dmrg_truncate_renormalize(dmrg_ctx* c, int32_t p, int32_t dir, in
     TruncResult tr = truncate_renormalize(*c, p, dir, M);
     if (trunc_err) *trunc_err = tr.trunc;
     if (kept) *kept = tr.kept;
+  });
+}
+
+extern "C" int dmrg_set_dbss(dmrg_ctx* c, int32_t M_min, double trunc_target) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(trunc_target <= 0.0 || (M_min >= 1 && trunc_target < 1.0), DMRG_EINVAL,
+                 "DBSS needs M_min >= 1 and 0 < trunc_target < 1");
+    c->dbss_min = trunc_target > 0.0 ? M_min : 0;
+    c->dbss_target = trunc_target > 0.0 ? trunc_target : 0.0;
   });
 }
 

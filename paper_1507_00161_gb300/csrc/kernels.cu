@@ -764,8 +764,12 @@ void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w
 // bitonic sort (descending) of w padded to np2 with -inf, in shared memory when it fits
 constexpr int64_t kKthSmem = 16384;
 
-__global__ void k_kth_largest(const double* __restrict__ w, int64_t n, int64_t k, double* gbuf,
-                              int64_t np2, double* out) {
+// out[0] = the k-th largest weight.  Fixed count (target <= 0): k = kmax.  Dynamic block
+// state selection (target > 0): k = the smallest count in [kmin, kmax] whose discarded
+// weight 1 - (w_1 + ... + w_k) (sorted descending, summed in that order in FP64) is at
+// most target, else kmax.  out[1] = k.
+__global__ void k_kth_largest(const double* __restrict__ w, int64_t n, int64_t kmax, int64_t kmin,
+                              double target, double* gbuf, int64_t np2, double* out) {
   extern __shared__ double kth_sm[];
   double* buf = np2 <= kKthSmem ? kth_sm : gbuf;
   for (int64_t i = threadIdx.x; i < np2; i += blockDim.x) buf[i] = i < n ? w[i] : -INFINITY;
@@ -786,10 +790,25 @@ __global__ void k_kth_largest(const double* __restrict__ w, int64_t n, int64_t k
       __syncthreads();
     }
   }
-  if (threadIdx.x == 0) out[0] = buf[k - 1];
+  if (threadIdx.x == 0) {
+    int64_t k = kmax;
+    if (target > 0.0) {
+      double kept = 0.0;
+      for (int64_t i = 0; i < kmax; ++i) {
+        kept += buf[i];
+        if (i + 1 >= kmin && 1.0 - kept <= target) {
+          k = i + 1;
+          break;
+        }
+      }
+    }
+    out[0] = buf[k - 1];
+    out[1] = double(k);
+  }
 }
-void kth_largest(const double* w, int64_t n, int64_t k, double* d_scratch, double* out,
-                 cudaStream_t s) {
+void kth_largest(const double* w, int64_t n, int64_t kmax, int64_t kmin, double target,
+                 double* d_scratch, double* out, cudaStream_t s) {
+  DMRG_REQUIRE(kmax >= 1 && kmax <= n && kmin >= 1, DMRG_EINVAL, "internal: bad selection count");
   int64_t np2 = 1;
   while (np2 < n) np2 <<= 1;
   static std::once_flag once;
@@ -798,7 +817,7 @@ void kth_largest(const double* w, int64_t n, int64_t k, double* d_scratch, doubl
                                    int(sizeof(double) * kKthSmem)));
   });
   const size_t smem = np2 <= kKthSmem ? sizeof(double) * size_t(np2) : 0;
-  k_kth_largest<<<1, 1024, smem, s>>>(w, n, k, d_scratch, np2, out);
+  k_kth_largest<<<1, 1024, smem, s>>>(w, n, kmax, kmin, target, d_scratch, np2, out);
   DMRG_LAUNCHED();
 }
 

@@ -95,10 +95,14 @@ def test_mixed_energy_is_fp64_accurate(P, space, Np, Nn, seed, M0):
     assert abs(e - e_ref) < 1e-8, (e, e_ref)
 
 
-def _compare_sweeps(P, prob, init, M, nsweeps):
-    o = _oracle(prob, init)
+def _compare_sweeps(P, prob, init, M, nsweeps, m_min=0, trunc_target=0.0):
+    from oracle.dmrg import OracleDMRG
+    o = OracleDMRG(prob, init, m_min=m_min, trunc_target=trunc_target)
     d = P.DMRG(prob)
     d.build_blocks(init)
+    if trunc_target > 0:
+        d.set_dbss(m_min, trunc_target)
+    kept_all = []
     for sw in range(nsweeps):
         ref = o.sweep(M)
         got, e_last = d.sweep(M)
@@ -107,6 +111,7 @@ def _compare_sweeps(P, prob, init, M, nsweeps):
             assert abs(r.energy - g["energy"]) < 1e-8, (sw, r.p, r.direction, r.energy, g["energy"])
             assert sum(r.kept.values()) == g["kept"], (sw, r.p, r.direction)
             assert abs(r.trunc_err - g["trunc_err"]) < 1e-9
+            kept_all.append(g["kept"])
         # block bases after the sweep: sectors and dimensions bit-exact
         for b in range(0, prob.n_sites - 2):
             if b in o.left:
@@ -120,6 +125,7 @@ def _compare_sweeps(P, prob, init, M, nsweeps):
                 blk = o.right[b]
                 assert [tuple(x) for x in qn] == blk.sectors
                 assert list(dims) == [blk.dims[q] for q in blk.sectors]
+    d.kept_all = kept_all
     return o, d
 
 
@@ -132,6 +138,35 @@ def test_sweeps_sd_shell_m64(P):
     """sd shell, 2p+2n (m-scheme dimension 640), M = 64."""
     prob = make_problem("sd", 2, 2, 0, seed=1)
     _compare_sweeps(P, prob, initial_mps(prob, 64, 5), 64, 2)
+
+
+@pytest.mark.parametrize("space,Np,Nn,seed,M0,M,m_min,target",
+                         [("p", 2, 2, 12, 5, 8, 3, 1e-3), ("sd", 2, 2, 1, 16, 64, 16, 1e-4),
+                          ("sd", 3, 2, 7, 24, 96, 8, 1e-5)])
+def test_dbss_sweeps(P, space, Np, Nn, seed, M0, M, m_min, target):
+    """Dynamic block state selection: per-step energies, kept counts, truncation errors
+    and block sectors against the oracle's DBSS sweeps."""
+    prob = make_problem(space, Np, Nn, 1 if (Np + Nn) % 2 else 0, seed=seed)
+    _, d = _compare_sweeps(P, prob, initial_mps(prob, M0, seed + 100), M, 2, m_min, target)
+    # the target, not the floor or the ceiling, decided some of the cuts
+    assert any(min(m_min, M) < k < M for k in d.kept_all)
+
+
+def test_dbss_arguments(P):
+    prob = make_problem("p", 2, 2, 0, seed=12)
+    d = P.DMRG(prob)
+    for m_min, target in ((4, 1.0), (4, float("nan")), (0, 1e-3)):
+        with pytest.raises(P.DmrgError) as e:
+            d.set_dbss(m_min, target)
+        assert e.value.code == P.DMRG_EINVAL
+    init = initial_mps(prob, 5, 5)
+    d.build_blocks(init)
+    d.set_dbss(4, 1e-3)
+    d.set_dbss(0, 0.0)         # back to a fixed M
+    got, _ = d.sweep(8)
+    ref = _oracle(prob, init).sweep(8)
+    assert [sum(r.kept.values()) for r in ref] == [g["kept"] for g in got]
+    assert max(abs(r.energy - g["energy"]) for r, g in zip(ref, got)) < 1e-8
 
 
 def test_full_m_reproduces_exact_diagonalization(P):
