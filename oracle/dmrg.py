@@ -291,6 +291,77 @@ def davidson(apply, diag, x0, tol=1e-8, max_iter=100, max_sub=24):
         Hs = Hn
 
 
+def davidson_roots(apply, diag, guesses, tol=1e-8, max_iter=100, max_sub=24, n_roots=2):
+    """The n_roots (1 or 2) lowest eigenpairs, for targeting several states at once (the
+    2+ excitation energies).  Same iteration as ``davidson``; the subspace starts from
+    the first guess, later guesses enter it before any correction; each iteration adds
+    the correction of the lowest root whose residual is above tol (root 0 while fewer
+    vectors than roots exist); stop when every root's residual is at most tol, or after
+    max_iter products.  Returns (thetas, normalised vectors, n_products, residuals)."""
+    x0 = guesses[0] / np.linalg.norm(guesses[0])
+    V = [x0]
+    AV = [apply(x0)]
+    nprod = 1
+    Hs = np.array([[V[0] @ AV[0]]])
+    pending = [g for g in guesses[1:n_roots]]
+    while True:
+        w, Y = np.linalg.eigh(Hs)
+        k = len(V)
+        xs, Axs, rs, rns = [], [], [], []
+        for j in range(min(n_roots, k)):
+            y = _sign_fix(Y[:, j])
+            x = sum(y[i] * V[i] for i in range(k))
+            Ax = sum(y[i] * AV[i] for i in range(k))
+            xs.append(x)
+            Axs.append(Ax)
+            rs.append(Ax - w[j] * x)
+            rns.append(float(np.linalg.norm(rs[-1])))
+        done = k >= n_roots and all(rn <= tol for rn in rns)
+        if done or nprod >= max_iter:
+            return ([float(v) for v in w[:len(xs)]], [x / np.linalg.norm(x) for x in xs], nprod,
+                    rns)
+        t = None
+        if pending:                       # a further guess, orthogonalised like a correction
+            t = pending.pop(0).copy()
+            tn0 = np.linalg.norm(t)
+            for _ in range(2):
+                for v in V:
+                    t = t - (v @ t) * v
+            if np.linalg.norm(t) <= 1e-14 * max(tn0, 1e-300):
+                t = None
+        if t is None:
+            j = next((j for j, rn in enumerate(rns) if rn > tol), 0)
+            den = w[j] - diag
+            small = np.abs(den) < 1e-8
+            den[small] = np.where(den[small] < 0, -1e-8, 1e-8)
+            t = rs[j] / den
+            if k >= max_sub:              # restart from the two lowest Ritz vectors
+                y1 = _sign_fix(Y[:, 1])
+                x1 = sum(y1[i] * V[i] for i in range(k))
+                Ax1 = sum(y1[i] * AV[i] for i in range(k))
+                V, AV = [xs[0], x1], [Axs[0], Ax1]
+                Hs = np.array([[w[0], 0.0], [0.0, w[1]]])
+            tn0 = np.linalg.norm(t)
+            for _ in range(2):
+                for v in V:
+                    t = t - (v @ t) * v
+            if np.linalg.norm(t) <= 1e-14 * max(tn0, 1e-300):
+                return ([float(v) for v in w[:len(xs)]], [x / np.linalg.norm(x) for x in xs],
+                        nprod, rns)
+        t = t / np.linalg.norm(t)
+        At = apply(t)
+        nprod += 1
+        k = len(V)
+        Hn = np.zeros((k + 1, k + 1))
+        Hn[:k, :k] = Hs
+        for i in range(k):
+            Hn[i, k] = Hn[k, i] = V[i] @ At
+        Hn[k, k] = t @ At
+        V.append(t)
+        AV.append(At)
+        Hs = Hn
+
+
 # ----------------------------------------------------------------------------------
 # truncation by the reduced density matrix
 # ----------------------------------------------------------------------------------
@@ -311,15 +382,18 @@ def truncate(psi: np.ndarray, lay: Layout, enl: Block, side: str, M: int, m_min:
              trunc_target: float = 0.0):
     """Returns (U per kept sector, kept count per sector, truncation error, eigenvalues).
 
-    trunc_target > 0 selects dynamically: M is the ceiling, m_min the floor, and the count
-    at the cut is ``dbss_count``; otherwise M states are kept."""
+    psi: one wave function, or several as the rows of a 2-D array (targeted states), whose
+    density matrices are averaged with equal weights.  trunc_target > 0 selects
+    dynamically: M is the ceiling, m_min the floor, and the count at the cut is
+    ``dbss_count``; otherwise M states are kept."""
+    vecs = [psi] if psi.ndim == 1 else list(psi)
     rho = {}
     for (QL, QR, dL, dR, off) in lay.blocks:
-        P = psi[off:off + dL * dR].reshape(dL, dR)
-        if side == "L":
-            rho[QL] = P @ P.T
-        else:
-            rho[QR] = P.T @ P
+        for v in vecs:
+            P = v[off:off + dL * dR].reshape(dL, dR)
+            part = (P @ P.T if side == "L" else P.T @ P) / len(vecs)
+            Q = QL if side == "L" else QR
+            rho[Q] = rho[Q] + part if Q in rho else part
     evals, evecs = {}, {}
     for Q in enl.sectors:
         d = enl.dims[Q]
@@ -367,12 +441,15 @@ class StepResult:
     residual: float
     trunc_err: float
     kept: Dict[tuple, int]
+    energy1: float = float("nan")     # second targeted state (two-state targeting)
 
 
 class OracleDMRG:
     def __init__(self, prob, init_mps, tol=1e-8, max_iter=100, max_sub=24, m_min=0,
-                 trunc_target=0.0):
+                 trunc_target=0.0, n_roots=1):
         self.m_min, self.trunc_target = m_min, trunc_target   # DBSS (trunc_target > 0)
+        self.n_roots = n_roots        # 2: the two lowest states targeted together
+        self.psi1 = None              # second targeted state of the last step
         self.ch = ch = ChainHamiltonian(prob)
         self.mpo = mpo = MPO(ch)
         self.N = N = ch.N
@@ -412,14 +489,16 @@ class OracleDMRG:
         Renl = enlarge_right(self.right[p + 1], p + 1, self.mpo, self.ch)
         return SuperBlock(Lenl, Renl, self.mpo.parity[p + 1], self.ch.target)
 
-    def _guess(self, p: int, direction: str, sb: SuperBlock) -> np.ndarray:
-        """White's prediction of the wave function at position p from the previous one."""
+    def _guess(self, p: int, direction: str, sb: SuperBlock, old=None) -> np.ndarray:
+        """White's prediction of the wave function at position p from the previous one
+        (``old``: another vector of the previous step, default its ground state)."""
         lay = sb.layout
         if self.psi is None:
             return np.ones(lay.size) / math.sqrt(max(lay.size, 1))
+        old = self.psi if old is None else old
         if self.psi_at[0] == p:
-            return self.psi.copy()
-        old, olay = self.psi, self.psi_layout
+            return old.copy()
+        olay = self.psi_layout
         new = np.zeros(lay.size)
         nidx = lay.index()
         q = self.ch.q
@@ -467,19 +546,35 @@ class OracleDMRG:
         sb = self.superblock(p)
         x0 = self._guess(p, direction, sb)
         diag = sb.diagonal()
-        theta, x, nprod, rn = davidson(sb.apply, diag, x0, self.tol, self.max_iter,
-                                       self.max_sub)
+        theta1, x1 = float("nan"), None
+        if self.n_roots == 1:
+            theta, x, nprod, rn = davidson(sb.apply, diag, x0, self.tol, self.max_iter,
+                                           self.max_sub)
+            target = x
+        else:
+            guesses = [x0]
+            if self.psi1 is not None:
+                guesses.append(self._guess(p, direction, sb, self.psi1))
+            th, xs, nprod, rns = davidson_roots(sb.apply, diag, guesses, self.tol,
+                                                self.max_iter, self.max_sub, 2)
+            if len(xs) < 2:
+                raise ValueError("superblock too small for two targeted states")
+            theta, theta1, x, x1, rn = th[0], th[1], xs[0], xs[1], max(rns)
+            target = np.stack([x, x1])
         if direction == "L":
-            U, keep, tr, _ = truncate(x, sb.layout, sb.L, "L", M, self.m_min, self.trunc_target)
+            U, keep, tr, _ = truncate(target, sb.layout, sb.L, "L", M, self.m_min,
+                                      self.trunc_target)
             self.UL[p] = U
             self.left[p] = project(sb.L, U)
         else:
-            U, keep, tr, _ = truncate(x, sb.layout, sb.R, "R", M, self.m_min, self.trunc_target)
+            U, keep, tr, _ = truncate(target, sb.layout, sb.R, "R", M, self.m_min,
+                                      self.trunc_target)
             self.UR[p] = U
             self.right[p] = project(sb.R, U)
         self.psi, self.psi_layout, self.psi_at = x, sb.layout, (p, direction)
+        self.psi1 = x1
         self._prev_L, self._prev_R = sb.L, sb.R
-        res = StepResult(p, direction, theta, nprod, rn, tr, keep)
+        res = StepResult(p, direction, theta, nprod, rn, tr, keep, theta1)
         self.history.append(res)
         return res
 

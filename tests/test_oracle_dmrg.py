@@ -231,3 +231,76 @@ def test_dbss_sweeps_bound_the_truncation_and_reach_exact():
         assert n_dbss < 0.5 * n_full
     assert abs(errs[0]) < 1e-9
     assert 1e-8 < errs[1] < 1e-3 and errs[2] > errs[1]
+
+
+# ---------------------------------------------------------------------------------------
+# two-state targeting: the two lowest states with the averaged density matrix
+# ---------------------------------------------------------------------------------------
+def test_two_root_davidson_reduces_to_one_root():
+    from oracle.dmrg import davidson, davidson_roots
+    sb, _ = _psi_at(3)
+    x0 = np.ones(sb.layout.size)
+    th, x, npr, rn = davidson(sb.apply, sb.diagonal(), x0, max_sub=6)
+    ths, xs, npr2, rns = davidson_roots(sb.apply, sb.diagonal(), [x0], max_sub=6, n_roots=1)
+    assert ths == [th] and npr2 == npr and rns == [rn]
+    assert np.array_equal(xs[0], x)
+
+
+@pytest.mark.parametrize("max_sub,second_guess", [(24, False), (5, False), (24, True)])
+def test_two_root_davidson_finds_the_two_lowest(max_sub, second_guess):
+    """Against the dense H_eff: both Ritz values are its two lowest eigenvalues, the
+    vectors are orthonormal eigenvectors (with and without restarts, with a second
+    guess entering the subspace)."""
+    from oracle.dmrg import davidson_roots
+    sb, _ = _psi_at(3)
+    n = sb.layout.size
+    He = np.stack([sb.apply(np.eye(n)[:, c]) for c in range(n)], axis=1)
+    ev, evec = np.linalg.eigh(He)
+    assert ev[1] - ev[0] > 1e-3 and ev[2] - ev[1] > 1e-3
+    rng = np.random.default_rng(4)
+    guesses = [np.ones(n)]
+    if second_guess:
+        guesses.append(evec[:, 1] + 1e-3 * rng.standard_normal(n))
+    ths, xs, npr, rns = davidson_roots(sb.apply, sb.diagonal(), guesses, tol=1e-10,
+                                       max_sub=max_sub, n_roots=2)
+    assert abs(ths[0] - ev[0]) < 1e-10 and abs(ths[1] - ev[1]) < 1e-10
+    assert max(rns) <= 1e-10
+    X = np.stack(xs, axis=1)
+    assert np.allclose(X.T @ X, np.eye(2), atol=1e-12)
+    assert np.linalg.norm(He @ X - X * np.array(ths)) < 1e-9
+
+
+def test_averaged_density_matrix_truncation():
+    """The two-state truncation keeps the largest eigenvalues of (rho_0 + rho_1) / 2,
+    obtained independently from the singular values of [P_0 P_1] / sqrt(2) per sector."""
+    from oracle.dmrg import davidson_roots, truncate
+    sb, _ = _psi_at(4)
+    ths, xs, _, _ = davidson_roots(sb.apply, sb.diagonal(), [np.ones(sb.layout.size)],
+                                   tol=1e-10, n_roots=2)
+    w = []
+    for (QL, QR, dL, dR, off) in sb.layout.blocks:
+        B = np.hstack([x[off:off + dL * dR].reshape(dL, dR) for x in xs]) / np.sqrt(2.0)
+        w.extend(np.linalg.svd(B, compute_uv=False) ** 2)
+    w = np.sort(np.concatenate([w, np.zeros(sum(sb.L.dims.values()) - len(w))]))[::-1]
+    assert abs(w.sum() - 1.0) < 1e-12
+    for M in (3, 6, 9):
+        _, keep, tr, _ = truncate(np.stack(xs), sb.layout, sb.L, "L", M)
+        assert sum(keep.values()) == M
+        assert abs(tr - w[M:].sum()) < 1e-12
+
+
+@pytest.mark.parametrize("space,seed,M0", [("p", 12, 6), ("sd", 1, 8)])
+def test_two_state_sweeps_reach_the_two_lowest_exact_states(space, seed, M0):
+    """Complete bases: the two targeted energies equal the two lowest eigenvalues of the
+    sector from exact diagonalization; truncated bases: both stay above them (the
+    projected Hamiltonian's eigenvalues interlace the exact ones)."""
+    p = make_problem(space, 2, 2, 0, seed=seed)
+    e0, e1 = ed_lowest(p, k=2)
+    d = OracleDMRG(p, initial_mps(p, M0, 5), n_roots=2)
+    res = d.sweep(10 ** 6)
+    res = d.sweep(10 ** 6)
+    assert abs(res[-1].energy - e0) < 1e-9 and abs(res[-1].energy1 - e1) < 1e-9
+    t = OracleDMRG(p, initial_mps(p, M0, 5), n_roots=2)
+    for _ in range(2):
+        for r in t.sweep(4 if space == "p" else 16):
+            assert r.energy >= e0 - 1e-10 and r.energy1 >= e1 - 1e-10
