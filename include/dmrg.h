@@ -97,6 +97,7 @@ typedef struct {
   double heff_flops;        /* algorithmic flops of one H_eff product                  */
   double heff_bytes;        /* algorithmic bytes of one H_eff product                  */
   double seconds;           /* wall time of the call                                   */
+  double energy1;           /* second targeted state (dmrg_set_roots(ctx, 2)), else NaN */
 } dmrg_dav_stats;
 
 typedef struct {
@@ -106,6 +107,7 @@ typedef struct {
   double heff_seconds;      /* device time of the H_eff products (CUDA events)         */
   double heff_flops;        /* algorithmic flops of one H_eff product at this position */
   double heff_bytes;        /* algorithmic bytes of one H_eff product                  */
+  double energy1;           /* second targeted state (dmrg_set_roots(ctx, 2)), else NaN */
 } dmrg_step_stats;
 
 /* Cumulative counters of a context since creation: kernel launches issued by the
@@ -201,6 +203,18 @@ int dmrg_step(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t M, dmrg_step_stats*
 /* One sweep = positions 1..N-3 left to right then N-3..1 back ("sweeping back and
  * forth").  steps: optional array of 2(N-3) records.  energy: energy of the last step. */
 int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy);
+
+/* Targeting of several states (the paper computes 2+ excitation energies by targeting the
+ * two lowest eigenstates at once, so that their errors cancel in the difference).
+ * n_roots = 1 (default) or 2.  With 2, every Davidson call seeks the two lowest
+ * eigenpairs of H_eff (the lowest state whose residual is above dav_tol is corrected;
+ * both must reach it), the truncation keeps the eigenvectors of the averaged reduced
+ * density matrix (rho_0 + rho_1) / 2, and both wave functions are carried to the next
+ * step by White's prediction.  The energies are returned in `energy` and `energy1` of
+ * the statistics records.  Needs DMRG_FP64 and DMRG_PRECOND_DIAG (DMRG_EINVAL
+ * otherwise, here and in dmrg_set_options while two states are targeted); not available
+ * in batch mode; a superblock with fewer than two states fails with DMRG_EINVAL. */
+int dmrg_set_roots(dmrg_ctx* ctx, int32_t n_roots);
 
 /* Dynamic block state selection (DBSS): the number of kept block states is set by the
  * truncation error instead of being fixed ("M_max determined by the truncation error

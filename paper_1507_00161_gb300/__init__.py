@@ -25,7 +25,8 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
-            "dmrg_set_options", "dmrg_set_dbss", "dmrg_get_counters", "dmrg_heff_cost",
+            "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_get_counters",
+            "dmrg_heff_cost",
             "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
             "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params",
             "dmrg_batch_create", "dmrg_batch_destroy", "dmrg_batch_last_error",
@@ -64,7 +65,7 @@ class DavStats(ctypes.Structure):
     _fields_ = [("n_products", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("residual", ctypes.c_double), ("energy", ctypes.c_double),
                 ("heff_flops", ctypes.c_double), ("heff_bytes", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("energy1", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):
@@ -72,7 +73,8 @@ class StepStats(ctypes.Structure):
                 ("kept", ctypes.c_int32), ("energy", ctypes.c_double),
                 ("residual", ctypes.c_double), ("trunc_err", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("heff_seconds", ctypes.c_double),
-                ("heff_flops", ctypes.c_double), ("heff_bytes", ctypes.c_double)]
+                ("heff_flops", ctypes.c_double), ("heff_bytes", ctypes.c_double),
+                ("energy1", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -128,6 +130,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_heff_cost": [P, i32, P, P, P],
         "dmrg_set_options": [P, ctypes.POINTER(Options)],
         "dmrg_set_dbss": [P, i32, dbl],
+        "dmrg_set_roots": [P, i32],
         "dmrg_mlp_reset": [P, ctypes.c_uint64],
         "dmrg_mlp_harvest": [P, i32, i32],
         "dmrg_mlp_train": [P, i32, i32, dbl, ctypes.c_uint64, P, P],
@@ -235,6 +238,11 @@ class DMRG:
                     stream=None, precond=PRECOND_DIAG):
         opt = self._options(precision, dav_tol, dav_max_iter, dav_max_sub, stream, precond)
         self._check(self.lib.dmrg_set_options(self.h, ctypes.byref(opt)))
+
+    def set_roots(self, n_roots):
+        """Target the n_roots (1 or 2) lowest states; with 2 the truncation averages
+        their density matrices and the second energy is reported as energy1."""
+        self._check(self.lib.dmrg_set_roots(self.h, int(n_roots)))
 
     def set_dbss(self, m_min, trunc_target):
         """Dynamic block state selection: M passed to the truncating calls becomes the

@@ -209,13 +209,17 @@ struct dmrg_ctx {
   std::unique_ptr<dmrg::Super> sb;
   dmrg::Prefetch pf;
   // Davidson workspace
-  dmrg::DevBuf<double> V, AV, r, t, x, Ax, x1, Ax1, small, partials;
+  dmrg::DevBuf<double> V, AV, r, t, x, Ax, x1, Ax1, r1, small, partials;
   dmrg::DevBuf<const double*> vptr;
   int64_t ws_n = 0, ws_sub = 0;
   // current eigenvector and what the next guess needs
   dmrg::DevBuf<double> psi, psi_guess;
   bool psi_valid = false;
   int psi_p = -1;
+  // two-state targeting: the second state of the last step and its predicted guess
+  int n_roots = 1;
+  dmrg::DevBuf<double> psi1, psi_guess1;
+  bool psi1_valid = false;
   std::unique_ptr<dmrg::Super> prev;   // layouts of the superblock psi belongs to
   // scratch
   dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
@@ -1402,6 +1406,7 @@ static void ensure_ws(Ctx& c, int64_t n, int sub) {
   c.Ax.alloc(nn);
   c.x1.alloc(nn);
   c.Ax1.alloc(nn);
+  c.r1.alloc(nn);
   c.small.alloc(64 * 64 * 6 + 1024);
   c.partials.alloc(64 * 300);
   std::vector<const double*> ptrs(2 * sub);
@@ -1448,6 +1453,7 @@ static void harvest(Ctx& c, Super& sb, int nhist, const double* psi) {
 
 struct DavResult {
   double theta = 0, resid = 0;
+  double theta1 = NAN, resid1 = 0;   // second state (two-state targeting)
   int nprod = 0;
   bool converged = false;
   double heff_seconds = 0;
@@ -1466,6 +1472,9 @@ struct DavRun {
   double* out = nullptr;
   double* px = nullptr;   // pending product: py = H_eff px
   double* py = nullptr;
+  int nroots = 1;                    // 2: the two lowest states
+  const double* guess1 = nullptr;    // second guess, enters the subspace first
+  double* out1 = nullptr;            // second state's vector
 };
 
 static const int kHist = 8;
@@ -1497,16 +1506,20 @@ static void dav_d2d(Ctx& c, double* dst, const double* src, int64_t n) {
   DMRG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
 }
 
-static void dav_begin(Ctx& c, Super& sb, const double* guess, double* out, DavRun& R) {
+static void dav_begin(Ctx& c, Super& sb, const double* guess, double* out, DavRun& R,
+                      const double* guess1 = nullptr, double* out1 = nullptr) {
   R = DavRun();
   R.sb = &sb;
   R.n = sb.size;
+  R.nroots = out1 ? 2 : 1;
+  R.guess1 = guess1;
+  R.out1 = out1;
   R.sub = std::max(4, std::min(64, c.opt.dav_max_sub));
   R.out = out;
   ensure_ws(c, R.n, R.sub);
   ensure_diag(c, sb);
   R.ld = c.ws_n;
-  R.use_mlp = c.opt.reserved0 == DMRG_PRECOND_MLP && c.mlp_trained;
+  R.use_mlp = c.opt.reserved0 == DMRG_PRECOND_MLP && c.mlp_trained && R.nroots == 1;
   if (c.mlp_harvest) {
     c.hist_x.alloc(kHist * R.ld);
     c.hist_r.alloc(kHist * R.ld);
@@ -1551,6 +1564,11 @@ static void dav_finish(Ctx& c, DavRun& R) {
   }
   (void)h;
   dav_d2d(c, R.out, c.x.p, n);
+  if (R.nroots == 2 && R.k >= 2) {
+    dot(c.x1.p, c.x1.p, n, P.sc + 8, P.part, c.stream);
+    scale_vec(c.x1.p, n, P.sc + 8, 1, c.stream);
+    dav_d2d(c, R.out1, c.x1.p, n);
+  }
   if (c.mlp_harvest && R.nhist > 0) harvest(c, sb, R.nhist, c.x.p);
   R.done = true;
   R.px = R.py = nullptr;
@@ -1576,11 +1594,25 @@ static void dav_after_product(Ctx& c, DavRun& R) {
   davidson_residual(c.x.p, c.Ax.p, P.w, n, c.r.p, s);
   dot(c.r.p, c.r.p, n, P.sc + 1, P.part, s);
   DMRG_CUDA(cudaMemcpyAsync(P.sc, P.w, sizeof(double), cudaMemcpyDeviceToDevice, s));
-  dav_readback(c, P.sc, 2, h);
+  // second state once the subspace holds two vectors: Ritz pair 1 and its residual
+  const bool two = R.nroots == 2 && R.k >= 2;
+  if (two) {
+    lincomb(P.Vp, P.Y + 64, R.k, n, c.x1.p, 0.0, 1.0, s);
+    lincomb(P.AVp, P.Y + 64, R.k, n, c.Ax1.p, 0.0, 1.0, s);
+    davidson_residual(c.x1.p, c.Ax1.p, P.w + 1, n, c.r1.p, s);
+    dot(c.r1.p, c.r1.p, n, P.sc + 3, P.part, s);   // sc[2..3] are free until the next step
+    DMRG_CUDA(cudaMemcpyAsync(P.sc + 2, P.w + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  dav_readback(c, P.sc, two ? 4 : 2, h);
   const double theta = h[0], rn = std::sqrt(std::max(h[1], 0.0));
   R.res.theta = theta;
   R.res.resid = rn;
   R.res.nprod = R.nprod;
+  const double rn1 = two ? std::sqrt(std::max(h[3], 0.0)) : 0.0;
+  if (two) {
+    R.res.theta1 = h[2];
+    R.res.resid1 = rn1;
+  }
   if (c.mlp_harvest && R.nhist < kHist) {   // iterate, residual and Ritz value for training
     dav_d2d(c, c.hist_x.p + R.nhist * ld, c.x.p, n);
     dav_d2d(c, c.hist_r.p + R.nhist * ld, c.r.p, n);
@@ -1591,13 +1623,35 @@ static void dav_after_product(Ctx& c, DavRun& R) {
   // FP32 products cannot resolve residuals below ~1e-7 of |H|: relative floor
   const double tol_eff =
       c.opt.precision == DMRG_FP64 ? tol : std::max(tol, 1e-6 * std::max(1.0, std::fabs(theta)));
-  if (rn <= tol_eff || R.nprod >= c.opt.dav_max_iter) {
-    R.res.converged = rn <= tol_eff;
+  const bool conv = rn <= tol_eff && (R.nroots == 1 || (two && rn1 <= tol_eff));
+  if (conv || R.nprod >= c.opt.dav_max_iter) {
+    R.res.converged = conv;
     dav_finish(c, R);
     return;
   }
-  // correction: t = r / (theta - D), clamped (diagonal), or the learned map
-  davidson_correction(c.r.p, sb.diag.p, P.w, n, c.t.p, s);
+  if (R.guess1 && R.k == 1) {   // the second guess enters the subspace before corrections
+    dav_d2d(c, c.t.p, R.guess1, n);
+    R.guess1 = nullptr;
+    dot(c.t.p, c.t.p, n, P.sc + 2, P.part, s);
+    for (int pass = 0; pass < 2; ++pass) {
+      multidot(P.Vp, R.k, c.t.p, n, P.sc + 32, P.part, s);
+      lincomb(P.Vp, P.sc + 32, R.k, n, c.t.p, 1.0, -1.0, s);
+    }
+    dot(c.t.p, c.t.p, n, P.sc + 3, P.part, s);
+    dav_readback(c, P.sc + 2, 2, h);
+    const double gn0 = std::sqrt(std::max(h[0], 0.0)), gn = std::sqrt(std::max(h[1], 0.0));
+    if (gn > 1e-14 * std::max(gn0, 1e-300)) {
+      dav_d2d(c, vec(R.k), c.t.p, n);
+      scale_vec(vec(R.k), n, P.sc + 3, 1, s);
+      R.px = vec(R.k);
+      R.py = avec(R.k);
+      return;
+    }
+  }
+  // correction of the lowest state whose residual is above the tolerance:
+  // t = r / (theta - D), clamped (diagonal), or the learned map
+  const int j = (two && rn <= tol_eff) ? 1 : 0;
+  davidson_correction(j ? c.r1.p : c.r.p, sb.diag.p, P.w + j, n, c.t.p, s);
   if (R.use_mlp) {
     double* fs = c.mlp_sc.p + 8;
     DMRG_CUDA(cudaMemcpyAsync(fs, P.w, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1675,10 +1729,11 @@ static void settle_energy(Ctx& c) {
 
 // defer_energy: leave the Rayleigh quotient of the mixed path running (dav_energy waits)
 static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out,
-                          bool defer_energy = false) {
+                          bool defer_energy = false, const double* guess1 = nullptr,
+                          double* out1 = nullptr) {
   PhaseTimer tm(c.t_davidson);
   DavRun R;
-  dav_begin(c, sb, guess, out, R);
+  dav_begin(c, sb, guess, out, R, guess1, out1);
   while (!R.done) {
     double t0 = wall();
     heff_timed(c, sb, R.px, R.py);
@@ -1708,6 +1763,8 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
   PhaseTimer tm(c.t_truncate);
   DMRG_REQUIRE(c.sb && c.sb->p == p && c.psi_valid && c.psi_p == p, DMRG_EINVAL,
                "no eigenvector held for this position (call dmrg_davidson first)");
+  DMRG_REQUIRE(c.n_roots == 1 || c.psi1_valid, DMRG_EINVAL,
+               "no second targeted state held for this position");
   DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
   DMRG_REQUIRE(M >= 1, DMRG_EINVAL, "M must be positive");
   Super& sb = *c.sb;
@@ -1735,17 +1792,24 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     tr.trunc = 0.0;
     tr.kept = int(total);
   } else {
+    // rho = psi psi^T per sector, or the average over the two targeted states
+    const bool two = c.n_roots == 2;
+    const double wgt = two ? 0.5 : 1.0;
     TaskList R;
     for (size_t b = 0; b < sb.bL.size(); ++b) {
       const int dL = sb.bdl[b], dR = sb.bdr[b];
       if (dir == 0) {
         const int Q = sb.bL[b];
         R.begin_task(Operand{roff[Q], B_Y, dL}, dL, dL);
-        R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dR, 2, 1.0);
+        R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dR, 2, wgt);
+        if (two)
+          R.add_term(Operand{sb.boff[b], B_Z, dR}, Operand{sb.boff[b], B_Z, dR}, dR, 2, wgt);
       } else {
         const int Q = sb.bR[b];
         R.begin_task(Operand{roff[Q], B_Y, dR}, dR, dR);
-        R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dL, 1, 1.0);
+        R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dL, 1, wgt);
+        if (two)
+          R.add_term(Operand{sb.boff[b], B_Z, dR}, Operand{sb.boff[b], B_Z, dR}, dL, 1, wgt);
       }
     }
     c.rho.alloc(sq);
@@ -1761,11 +1825,13 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
       int64_t be[NBASE] = {0};
       be[B_X] = sb.size;
       be[B_Y] = sq;
+      if (two) be[B_Z] = sb.size;
       dR.build(R, be, s);
     }
     Bases<double> bb{};
     bb.p[B_X] = c.psi.p;
     bb.p[B_Y] = c.rho.p;
+    if (two) bb.p[B_Z] = c.psi1.p;
     run_gemm_tasks<double>(dR, bb, 1, s);
     int maxd = 0;
     for (int x : dims) maxd = std::max(maxd, x);
@@ -1831,9 +1897,11 @@ static void uniform_guess(Ctx& c, Super& sb, double* g) {
   fill_value(g, sb.size, 1.0 / std::sqrt(double(std::max<int64_t>(sb.size, 1))), c.stream);
 }
 
-static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
+// src: a vector of the previous step (its ground state by default)
+static void predict(Ctx& c, Super& sb, int p, int dir, double* g, const double* src = nullptr) {
   PhaseTimer tm(c.t_predict);
   cudaStream_t s = c.stream;
+  if (!src) src = c.psi.p;
   if (!c.psi_valid || !c.prev) {
     uniform_guess(c, sb, g);
     return;
@@ -1841,7 +1909,7 @@ static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
   Super& pr = *c.prev;
   if (pr.p == p) {
     DMRG_REQUIRE(pr.size == sb.size, DMRG_EINVAL, "internal: layout changed at turn");
-    DMRG_CUDA(cudaMemcpyAsync(g, c.psi.p, sizeof(double) * sb.size, cudaMemcpyDeviceToDevice, s));
+    DMRG_CUDA(cudaMemcpyAsync(g, src, sizeof(double) * sb.size, cudaMemcpyDeviceToDevice, s));
     return;
   }
   TaskList A, B;
@@ -1934,7 +2002,7 @@ static void predict(Ctx& c, Super& sb, int p, int dir, double* g) {
     dA.build(A, be, s);
     dB.build(B, be, s);
   }
-  bb.p[B_X] = c.psi.p;
+  bb.p[B_X] = const_cast<double*>(src);   // read only
   bb.p[B_T] = c.tmp.p;
   bb.p[B_Y] = g;
   run_gemm_tasks<double>(dA, bb, 1, s);
@@ -2059,10 +2127,22 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st,
   else if (dir == 1 && p - 2 >= 0 && c.left[p - 2].valid)
     start_prefetch(c, c.left[p - 2].ops, c.left[p - 2].gen, p - 1, true);
   c.psi_guess.alloc(std::max<int64_t>(sb.size, 1));
+  const bool two = c.n_roots == 2;
+  const bool pred1 = two && c.psi1_valid && c.psi_valid && c.prev;
+  if (pred1) {   // White's prediction of the second state through the same bases
+    c.psi_guess1.alloc(std::max<int64_t>(sb.size, 1));
+    predict(c, sb, p, dir, c.psi_guess1.p, c.psi1.p);
+  }
   predict(c, sb, p, dir, c.psi_guess.p);
   c.psi.alloc(std::max<int64_t>(sb.size, 1));
+  if (two) c.psi1.alloc(std::max<int64_t>(sb.size, 1));
   settle_energy(c);   // the previous step's energy (its product reads vectors Davidson reuses)
-  DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p, true);
+  c.psi1_valid = false;
+  DavResult r = davidson(c, sb, c.psi_guess.p, c.psi.p, true, pred1 ? c.psi_guess1.p : nullptr,
+                         two ? c.psi1.p : nullptr);
+  DMRG_REQUIRE(!two || !std::isnan(r.theta1), DMRG_EINVAL,
+               "the superblock holds fewer states than the two targeted ones");
+  c.psi1_valid = two;
   if (dir == 0 && p + 2 <= c.N - 2 && c.right[p + 2].valid) issue_prefetch_device(c, c.right[p + 2].ops);
   else if (dir == 1 && p - 2 >= 0 && c.left[p - 2].valid) issue_prefetch_device(c, c.left[p - 2].ops);
   const double flops = sb.flops, bytes = sb.bytes;
@@ -2077,9 +2157,10 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st,
     st->n_products = r.nprod;
     st->kept = tr.kept;
     st->energy = r.theta;
-    st->residual = r.resid;
+    st->residual = std::max(r.resid, r.resid1);
     st->trunc_err = tr.trunc;
     st->seconds = now_s() - t0;
+    st->energy1 = r.theta1;
     st->heff_seconds = r.heff_seconds;
     st->heff_flops = flops;
     st->heff_bytes = bytes;
@@ -2250,15 +2331,28 @@ extern "C" int dmrg_davidson(dmrg_ctx* c, int32_t p, const double* guess, double
     double t0 = now_s();
     Super& sb = super_at(*c, p);
     c->psi_guess.alloc(std::max<int64_t>(sb.size, 1));
+    const int pdir = (c->prev && c->prev->p > p) ? 1 : 0;
+    const bool two = c->n_roots == 2;
+    const bool pred1 = two && !guess && c->psi1_valid && c->psi_valid && c->prev;
+    if (pred1) {
+      c->psi_guess1.alloc(std::max<int64_t>(sb.size, 1));
+      predict(*c, sb, p, pdir, c->psi_guess1.p, c->psi1.p);
+    }
     if (guess) {
       DMRG_CUDA(cudaMemcpyAsync(c->psi_guess.p, guess, sizeof(double) * sb.size,
                                 cudaMemcpyDeviceToDevice, c->stream));
     } else {
-      predict(*c, sb, p, (c->prev && c->prev->p > p) ? 1 : 0, c->psi_guess.p);
+      predict(*c, sb, p, pdir, c->psi_guess.p);
     }
     c->psi.alloc(std::max<int64_t>(sb.size, 1));
-    DavResult r = davidson(*c, sb, c->psi_guess.p, c->psi.p);
+    if (two) c->psi1.alloc(std::max<int64_t>(sb.size, 1));
+    c->psi1_valid = false;
+    DavResult r = davidson(*c, sb, c->psi_guess.p, c->psi.p, false,
+                           pred1 ? c->psi_guess1.p : nullptr, two ? c->psi1.p : nullptr);
+    DMRG_REQUIRE(!two || !std::isnan(r.theta1), DMRG_EINVAL,
+                 "the superblock holds fewer states than the two targeted ones");
     c->psi_valid = true;
+    c->psi1_valid = two;
     c->psi_p = p;
     if (out) {
       DMRG_CUDA(cudaMemcpyAsync(out, c->psi.p, sizeof(double) * sb.size, cudaMemcpyDeviceToDevice,
@@ -2269,11 +2363,12 @@ extern "C" int dmrg_davidson(dmrg_ctx* c, int32_t p, const double* guess, double
     if (st) {
       st->n_products = r.nprod;
       st->converged = r.converged ? 1 : 0;
-      st->residual = r.resid;
+      st->residual = std::max(r.resid, r.resid1);
       st->energy = r.theta;
       st->heff_flops = sb.flops;
       st->heff_bytes = sb.bytes;
       st->seconds = now_s() - t0;
+      st->energy1 = r.theta1;
     }
     conv = r.converged ? 1 : 0;
   });
@@ -2290,6 +2385,17 @@ extern "C" int dmrg_truncate_renormalize(dmrg_ctx* c, int32_t p, int32_t dir, in
     TruncResult tr = truncate_renormalize(*c, p, dir, M);
     if (trunc_err) *trunc_err = tr.trunc;
     if (kept) *kept = tr.kept;
+  });
+}
+
+extern "C" int dmrg_set_roots(dmrg_ctx* c, int32_t n_roots) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(n_roots == 1 || n_roots == 2, DMRG_EINVAL, "n_roots must be 1 or 2");
+    DMRG_REQUIRE(n_roots == 1 || (c->opt.precision == DMRG_FP64 &&
+                                  c->opt.reserved0 == DMRG_PRECOND_DIAG),
+                 DMRG_EINVAL, "two-state targeting needs DMRG_FP64 and the diagonal preconditioner");
+    if (n_roots != c->n_roots) c->psi1_valid = false;
+    c->n_roots = n_roots;
   });
 }
 
@@ -2354,6 +2460,9 @@ extern "C" int dmrg_set_options(dmrg_ctx* c, const dmrg_options* opt) {
     DMRG_REQUIRE(opt->dav_tol > 0 && opt->dav_max_iter >= 1 && opt->dav_max_sub >= 4 &&
                      opt->dav_max_sub <= 64,
                  DMRG_EINVAL, "bad Davidson options");
+    DMRG_REQUIRE(c->n_roots == 1 || (opt->precision == DMRG_FP64 &&
+                                     opt->reserved0 == DMRG_PRECOND_DIAG),
+                 DMRG_EINVAL, "two-state targeting needs DMRG_FP64 and the diagonal preconditioner");
     const bool prec_changed = opt->precision != c->opt.precision;
     c->opt = *opt;
     c->stream = static_cast<cudaStream_t>(opt->stream);
@@ -2815,6 +2924,7 @@ static void batch_step(dmrg_batch& B, const std::vector<BWork>& work,
     s.heff_seconds = 0;
     s.heff_flops = flops;
     s.heff_bytes = bytes;
+    s.energy1 = NAN;
   });
 }
 
@@ -2888,6 +2998,8 @@ extern "C" int dmrg_batch_sweep(dmrg_batch* b, const int32_t* M, double* energie
       DMRG_REQUIRE(b->ctx[i]->opt.precision == b->precision, DMRG_EINVAL,
                    "all contexts of a batch must use the same precision");
       DMRG_REQUIRE(M[i] >= 1, DMRG_EINVAL, "M must be positive");
+      DMRG_REQUIRE(b->ctx[i]->n_roots == 1, DMRG_EINVAL,
+                   "two-state targeting is not available in batch mode");
     }
     std::vector<std::vector<std::pair<int, int>>> seq(n);
     size_t len = 0;

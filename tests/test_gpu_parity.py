@@ -95,13 +95,15 @@ def test_mixed_energy_is_fp64_accurate(P, space, Np, Nn, seed, M0):
     assert abs(e - e_ref) < 1e-8, (e, e_ref)
 
 
-def _compare_sweeps(P, prob, init, M, nsweeps, m_min=0, trunc_target=0.0):
+def _compare_sweeps(P, prob, init, M, nsweeps, m_min=0, trunc_target=0.0, n_roots=1):
     from oracle.dmrg import OracleDMRG
-    o = OracleDMRG(prob, init, m_min=m_min, trunc_target=trunc_target)
+    o = OracleDMRG(prob, init, m_min=m_min, trunc_target=trunc_target, n_roots=n_roots)
     d = P.DMRG(prob)
     d.build_blocks(init)
     if trunc_target > 0:
         d.set_dbss(m_min, trunc_target)
+    if n_roots > 1:
+        d.set_roots(n_roots)
     kept_all = []
     for sw in range(nsweeps):
         ref = o.sweep(M)
@@ -109,6 +111,10 @@ def _compare_sweeps(P, prob, init, M, nsweeps, m_min=0, trunc_target=0.0):
         for r, g in zip(ref, got):
             assert (r.p, 0 if r.direction == "L" else 1) == (g["p"], g["dir"])
             assert abs(r.energy - g["energy"]) < 1e-8, (sw, r.p, r.direction, r.energy, g["energy"])
+            if n_roots > 1:
+                assert abs(r.energy1 - g["energy1"]) < 1e-8, (sw, r.p, r.direction)
+            else:
+                assert np.isnan(g["energy1"])
             assert sum(r.kept.values()) == g["kept"], (sw, r.p, r.direction)
             assert abs(r.trunc_err - g["trunc_err"]) < 1e-9
             kept_all.append(g["kept"])
@@ -167,6 +173,56 @@ def test_dbss_arguments(P):
     ref = _oracle(prob, init).sweep(8)
     assert [sum(r.kept.values()) for r in ref] == [g["kept"] for g in got]
     assert max(abs(r.energy - g["energy"]) for r, g in zip(ref, got)) < 1e-8
+
+
+@pytest.mark.parametrize("space,Np,Nn,seed,M0,M,nsweeps",
+                         [("p", 2, 2, 12, 5, 8, 3), ("sd", 3, 2, 7, 24, 48, 2)])
+def test_two_state_sweeps(P, space, Np, Nn, seed, M0, M, nsweeps):
+    """Two lowest states targeted together (averaged density matrix): both energies of
+    every step, kept counts, truncation errors and block sectors against the oracle."""
+    prob = make_problem(space, Np, Nn, 1 if (Np + Nn) % 2 else 0, seed=seed)
+    _compare_sweeps(P, prob, initial_mps(prob, M0, seed + 100), M, nsweeps, n_roots=2)
+
+
+def test_two_state_full_m_gives_the_two_lowest_exact_states(P):
+    from oracle.hamiltonian import ed_lowest
+    prob = make_problem("sd", 2, 2, 0, seed=1)
+    e0, e1 = ed_lowest(prob, k=2)
+    d = P.DMRG(prob)
+    d.build_blocks(initial_mps(prob, 8, 5))
+    d.set_roots(2)
+    d.sweep(400)
+    steps, e = d.sweep(400)
+    assert abs(steps[-1]["energy"] - e0) < 1e-9 and abs(steps[-1]["energy1"] - e1) < 1e-9
+    # the single-state Davidson at the same position agrees on the ground state
+    d.set_roots(1)
+    e_single, st = d.davidson(1)
+    assert abs(e_single - e0) < 1e-9 and np.isnan(st["energy1"])
+
+
+def test_two_state_arguments(P):
+    prob = make_problem("p", 2, 2, 0, seed=12)
+    d = P.DMRG(prob)
+    for bad in (0, 3):
+        with pytest.raises(P.DmrgError) as e:
+            d.set_roots(bad)
+        assert e.value.code == P.DMRG_EINVAL
+    d.set_options(precision=P.MIXED_FP32)
+    with pytest.raises(P.DmrgError) as e:
+        d.set_roots(2)
+    assert e.value.code == P.DMRG_EINVAL
+    d.set_options(precision=P.FP64)
+    d.set_roots(2)
+    with pytest.raises(P.DmrgError) as e:
+        d.set_options(precision=P.MIXED_FP32)
+    assert e.value.code == P.DMRG_EINVAL
+    # dmrg_davidson alone reports both states
+    d.build_blocks(initial_mps(prob, 5, 5))
+    from oracle.dmrg import davidson_roots
+    sb = _oracle(prob, initial_mps(prob, 5, 5)).superblock(1)
+    th, _, _, _ = davidson_roots(sb.apply, sb.diagonal(), [np.ones(sb.layout.size)], n_roots=2)
+    e, st = d.davidson(1)
+    assert abs(e - th[0]) < 1e-8 and abs(st["energy1"] - th[1]) < 1e-8
 
 
 def test_full_m_reproduces_exact_diagonalization(P):
