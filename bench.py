@@ -321,6 +321,63 @@ def run_precond_compare(P):
             "max_dE": dmax}
 
 
+def run_next_rows(P, prob, init, M, e_fixed):
+    """Rows beyond the core path, each timed once by wall clock around a whole sweep:
+    dynamic block state selection on the default workload (mixed path, M_min = 256,
+    ceiling M, discarded-weight target 1e-5; compared with the fixed-M sweep from the same
+    starting state), and two-state targeting on pf 4p+4n at M = 1024 in FP64 (one state
+    vs the two lowest, from the same starting state)."""
+    import torch
+    from gen import make_problem, initial_mps
+    out = {}
+    try:
+        d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8)
+        d.build_blocks(init)
+        d.set_dbss(256, 1e-5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, e = d.sweep(M)
+        torch.cuda.synchronize()
+        kept = [s["kept"] for s in steps]
+        out["dbss"] = {"workload": "default workload, M_min=256, M_max=%d, target 1e-5, one "
+                                   "sweep from the starting state, mixed path" % M,
+                       "sweep_s": time.perf_counter() - t0, "energy": e,
+                       "dE_vs_fixed_M": e - e_fixed if e_fixed is not None else None,
+                       "kept_min": min(kept), "kept_max": max(kept),
+                       "kept_mean": sum(kept) / len(kept),
+                       "trunc_err_max": max(s["trunc_err"] for s in steps),
+                       "products": sum(s["n_products"] for s in steps)}
+        d.close()
+    except Exception as exc:          # a side measurement never takes the bench line down
+        out["dbss"] = {"error": str(exc)}
+    try:
+        prob2 = make_problem("pf", 4, 4, 0, seed=2)
+        init2 = initial_mps(prob2, 1024, 2002)
+        res = {}
+        for n_roots in (1, 2):
+            d = P.DMRG(prob2, precision=P.FP64, dav_tol=1e-8)
+            d.build_blocks(init2)
+            d.set_roots(n_roots)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, _ = d.sweep(1024)
+            torch.cuda.synchronize()
+            res[n_roots] = (time.perf_counter() - t0, steps)
+            d.close()
+        s1, s2 = res[1][1], res[2][1]
+        out["two_state"] = {"workload": "pf 4p+4n seed 2, M=1024, FP64, one sweep from the "
+                                        "same starting state",
+                            "one_state_sweep_s": res[1][0], "two_state_sweep_s": res[2][0],
+                            "products_one": sum(s["n_products"] for s in s1),
+                            "products_two": sum(s["n_products"] for s in s2),
+                            "E0": s2[-1]["energy"], "E1": s2[-1]["energy1"],
+                            "excitation": s2[-1]["energy1"] - s2[-1]["energy"],
+                            "E0_one_state": s1[-1]["energy"]}
+    except Exception as exc:
+        out["two_state"] = {"error": str(exc)}
+    return out
+
+
 def run_gpu(args):
     import ctypes
     import numpy as np
@@ -443,6 +500,9 @@ def run_gpu(args):
     if args.batch_mcap > 0:
         batch = run_batch_compare(P, args.batch_mcap)
     precond = run_precond_compare(P) if args.precond else None
+    next_rows = None
+    if args.next_rows:
+        next_rows = run_next_rows(P, prob, init, M, e2e["sweep_energy"] if e2e else None)
     if rank != 0:
         return 0
     cpu = None
@@ -473,6 +533,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "batch": batch,
         "precond": precond,
+        "next_rows": next_rows,
         "e2e": e2e,
         "gpu_launches": int(c1["launches"] - c0["launches"]),
         "device_mem_used_gb": dev_used_gb,
@@ -509,6 +570,8 @@ def main():
                     help="M cap of the 32-instance batch-vs-loop comparison (0: skip)")
     ap.add_argument("--precond", type=int, default=1,
                     help="learned vs diagonal preconditioner comparison (0: skip)")
+    ap.add_argument("--next-rows", type=int, default=1,
+                    help="also time a DBSS sweep and a two-state sweep (side measurements)")
     ap.add_argument("--workload", default="",
                     help="space:Np:Nn:seed of another system (profiling of smaller cases)")
     ap.add_argument("--profile-range", action="store_true",
