@@ -19,6 +19,10 @@ Contents and pins (each checked by a ``-m "not gpu"`` test):
   H_eff on exact states, and truncation error -> 0 at full M.  Its dynamic block state
   selection is pinned by brute force on singular values of the wave-function blocks,
   by its reductions to the fixed-M rule, and by the truncation bound along sweeps.
+* ``entropy``: two-orbital density matrix of the dot orbitals and the one- and
+  two-orbital entropies.  Pinned by the exact ground state in the determinant basis
+  (occupations, pair occupations, the hopping element with determinant signs) and by
+  equal entropies of time-reversed orbitals.
 * ``extrapolate``: least-squares E(M) fits.  Pinned by exact model data, the normal
   equations, an independent exponent scan and equivariance under shift and scale.
 """
