@@ -216,6 +216,20 @@ int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy)
  * in batch mode; a superblock with fewer than two states fails with DMRG_EINVAL. */
 int dmrg_set_roots(dmrg_ctx* ctx, int32_t n_roots);
 
+/* Orbital entropies of the two dots (the one-orbital entropy s_i = -Tr rho_i ln rho_i and
+ * the two-orbital mutual information of the paper's entanglement analysis) from the
+ * wave function held for position p (after dmrg_davidson, dmrg_step or a sweep that ended
+ * at p), on the device.  rho: optional host array of 16, the two-orbital reduced density
+ * matrix of chain positions p and p+1, row-major, basis index 2 n_p + n_{p+1} (|00>,
+ * |01>, |10>, |11>), rho[a][b] = sum_{l,r} psi(l,a,r) psi(l,b,r); it is diagonal except
+ * for the |01>,|10> element, which equals <c+_{p+1} c_p> and is nonzero only when the two
+ * orbitals have equal (species, m).  ent: optional host array of 4: s_p, s_{p+1}, the
+ * two-orbital entropy s_{p,p+1} and the mutual information I = s_p + s_{p+1} - s_{p,p+1}
+ * (natural logarithms; I >= 0, the paper prints the opposite sign convention).  A sweep
+ * therefore gives s_i of every orbital at chain positions 1..N-2 and I of every
+ * neighbouring pair.  DMRG_EINVAL if no wave function is held for p. */
+int dmrg_dot_rdm(dmrg_ctx* ctx, int32_t p, double* rho, double* ent);
+
 /* Dynamic block state selection (DBSS): the number of kept block states is set by the
  * truncation error instead of being fixed ("M_max determined by the truncation error
  * delta eps_TR" of the method section; the paper's runs use M_min = 256 and delta eps_TR =

@@ -25,7 +25,8 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
-            "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_get_counters",
+            "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_dot_rdm",
+            "dmrg_get_counters",
             "dmrg_heff_cost",
             "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
             "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params",
@@ -131,6 +132,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_set_options": [P, ctypes.POINTER(Options)],
         "dmrg_set_dbss": [P, i32, dbl],
         "dmrg_set_roots": [P, i32],
+        "dmrg_dot_rdm": [P, i32, P, P],
         "dmrg_mlp_reset": [P, ctypes.c_uint64],
         "dmrg_mlp_harvest": [P, i32, i32],
         "dmrg_mlp_train": [P, i32, i32, dbl, ctypes.c_uint64, P, P],
@@ -243,6 +245,14 @@ class DMRG:
         """Target the n_roots (1 or 2) lowest states; with 2 the truncation averages
         their density matrices and the second energy is reported as energy1."""
         self._check(self.lib.dmrg_set_roots(self.h, int(n_roots)))
+
+    def dot_rdm(self, p):
+        """Two-orbital density matrix (4 x 4) of chain positions p, p+1 from the wave
+        function held for p, and (s_p, s_{p+1}, s_{p,p+1}, I_{p,p+1})."""
+        rho = np.zeros(16)
+        ent = np.zeros(4)
+        self._check(self.lib.dmrg_dot_rdm(self.h, int(p), _np_ptr(rho), _np_ptr(ent)))
+        return rho.reshape(4, 4), tuple(float(x) for x in ent)
 
     def set_dbss(self, m_min, trunc_target):
         """Dynamic block state selection: M passed to the truncating calls becomes the

@@ -358,6 +358,15 @@ void batched_eigh2(const int64_t* d_off, const int64_t* d_woff, const int32_t* d
                    cudaStream_t s);
 void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w, double* d_Y,
                 cudaStream_t s);
+// a piece of a wave-function block paired with another (or itself): the sum over
+// i < nr, j < nc of psi[a + i lda + j] psi[b + i ldb + j] goes to sum number slot (0..4)
+struct RdmTask {
+  int64_t a, b;
+  int32_t lda, ldb, nr, nc, slot, pad;
+};
+// the five sums of the dot density matrix; d_part holds one double per task
+void rdm_sums(const RdmTask* d_tasks, int64_t n, const double* psi, double* d_part,
+              double* d_out, cudaStream_t s);
 // global selection: k-th largest of w[0..n) (ties irrelevant for the value) in out[0] and k
 // in out[1]; k = kmax, or with target > 0 the smallest k in [kmin, kmax] whose discarded
 // weight 1 - (sum of the k largest) is at most target (kmax if none)

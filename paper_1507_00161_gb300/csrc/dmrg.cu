@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <exception>
 #include <functional>
+#include <initializer_list>
 #include <memory>
 #include <mutex>
 #include <set>
@@ -2385,6 +2386,91 @@ extern "C" int dmrg_truncate_renormalize(dmrg_ctx* c, int32_t p, int32_t dir, in
     TruncResult tr = truncate_renormalize(*c, p, dir, M);
     if (trunc_err) *trunc_err = tr.trunc;
     if (kept) *kept = tr.kept;
+  });
+}
+
+extern "C" int dmrg_dot_rdm(dmrg_ctx* c, int32_t p, double* rho, double* ent) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(c->psi_valid && c->psi_p == p, DMRG_EINVAL,
+                 "no wave function held for this position (run dmrg_davidson or dmrg_step)");
+    Super* sb = (c->sb && c->sb->p == p) ? c->sb.get()
+                                          : (c->prev && c->prev->p == p ? c->prev.get() : nullptr);
+    DMRG_REQUIRE(sb != nullptr, DMRG_EINVAL, "the layout of the held wave function is gone");
+    const Layout& Ll = sb->Ll;
+    const Layout& Rl = sb->Rl;
+    // rows (columns) of piece sigma of an enlarged sector: pieces are contiguous, state 0 first
+    auto extent = [](const Layout& L, int Q, int sg, int* off, int* len) {
+      if (L.pblk[Q][sg] < 0) return false;
+      const int D = L.sec.d[Q];
+      *off = L.poff[Q][sg];
+      *len = (sg == 0 && L.pblk[Q][1] >= 0 ? L.poff[Q][1] : D) - *off;
+      return *len > 0;
+    };
+    std::vector<RdmTask> tasks;
+    for (size_t b = 0; b < sb->bL.size(); ++b) {
+      const int QL = sb->bL[b], QR = sb->bR[b], dR = sb->bdr[b];
+      for (int sl = 0; sl < 2; ++sl)
+        for (int sr = 0; sr < 2; ++sr) {
+          int ro, nr, co, nc;
+          if (!extent(Ll, QL, sl, &ro, &nr) || !extent(Rl, QR, sr, &co, &nc)) continue;
+          const int64_t a = sb->boff[b] + int64_t(ro) * dR + co;
+          tasks.push_back(RdmTask{a, a, dR, dR, nr, nc, 2 * sl + sr, 0});
+        }
+    }
+    // the hop between dots of equal quantum numbers: psi(l, 1, 0, r) psi(l, 0, 1, r)
+    const QN qs = c->chain.q[p];
+    if (qs == c->chain.q[p + 1]) {
+      for (size_t b = 0; b < sb->bL.size(); ++b) {
+        const int QL = sb->bL[b], QR = sb->bR[b], dR = sb->bdr[b];
+        int ro, nr, co, nc;
+        if (!extent(Ll, QL, 1, &ro, &nr) || !extent(Rl, QR, 0, &co, &nc)) continue;
+        const int QL2 = Ll.sec.find(Ll.sec.q[QL] - qs);
+        if (QL2 < 0 || Ll.pblk[QL2][0] != Ll.pblk[QL][1]) continue;
+        const int b2 = sb->psi_of_L[QL2];
+        if (b2 < 0) continue;
+        const int QR2 = sb->bR[b2];
+        if (Rl.sec.q[QR2] != Rl.sec.q[QR] + qs || Rl.pblk[QR2][1] != Rl.pblk[QR][0]) continue;
+        int ro2, nr2, co2, nc2;
+        if (!extent(Ll, QL2, 0, &ro2, &nr2) || !extent(Rl, QR2, 1, &co2, &nc2)) continue;
+        DMRG_REQUIRE(nr2 == nr && nc2 == nc, DMRG_EINVAL, "internal: hop pieces differ in size");
+        const int dR2 = sb->bdr[b2];
+        tasks.push_back(RdmTask{sb->boff[b] + int64_t(ro) * dR + co,
+                                sb->boff[b2] + int64_t(ro2) * dR2 + co2, dR, dR2, nr, nc, 4, 0});
+      }
+    }
+    for (const RdmTask& t : tasks)   // every piece inside the wave function
+      DMRG_REQUIRE(t.a >= 0 && t.b >= 0 && t.a + int64_t(t.nr - 1) * t.lda + t.nc <= sb->size &&
+                       t.b + int64_t(t.nr - 1) * t.ldb + t.nc <= sb->size,
+                   DMRG_EINVAL, "internal: density-matrix piece outside the wave function");
+    DevBuf<RdmTask> dt;
+    DevBuf<double> part, sums;
+    dt.upload(tasks, c->stream);
+    part.alloc(std::max<int64_t>(int64_t(tasks.size()), 1));
+    sums.alloc(8);
+    rdm_sums(dt.p, int64_t(tasks.size()), c->psi.p, part.p, sums.p, c->stream);
+    double h[5];
+    dav_readback(*c, sums.p, 5, h);
+    double r[16] = {0};
+    for (int k = 0; k < 4; ++k) r[5 * k] = h[k];
+    r[6] = r[9] = h[4];
+    if (rho) std::copy(r, r + 16, rho);
+    if (ent) {
+      auto vn = [](std::initializer_list<double> w) {
+        double s = 0.0;
+        for (double x : w)
+          if (x > 0.0) s -= x * std::log(x);
+        return s;
+      };
+      const double sp = vn({h[0] + h[1], h[2] + h[3]});
+      const double sq = vn({h[0] + h[2], h[1] + h[3]});
+      const double mid = 0.5 * (h[1] + h[2]);
+      const double rad = std::sqrt(0.25 * (h[1] - h[2]) * (h[1] - h[2]) + h[4] * h[4]);
+      const double spq = vn({h[0], h[3], mid + rad, mid - rad});
+      ent[0] = sp;
+      ent[1] = sq;
+      ent[2] = spq;
+      ent[3] = sp + sq - spq;
+    }
   });
 }
 

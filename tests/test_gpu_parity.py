@@ -276,3 +276,41 @@ def test_fused_product_matches_two_stage(P):
         checked += 1
     assert checked >= 4
     assert max_dl > 32 and max_dr > 32, (max_dl, max_dr)
+
+
+def _by_m(prob):
+    keys = sorted(range(prob.n_sites),
+                  key=lambda s: (int(prob.species[s]), int(prob.two_m[s]), int(prob.orbital[s])))
+    return prob.with_order(keys)
+
+
+@pytest.mark.parametrize("space,Np,Nn,two_M,seed,M0,M,by_m",
+                         [("p", 2, 1, 1, 3, 5, 8, True), ("sd", 2, 2, 0, 1, 16, 64, False),
+                          ("sd", 3, 2, 3, 7, 24, 48, True)])
+def test_dot_rdm_along_a_sweep(P, space, Np, Nn, two_M, seed, M0, M, by_m):
+    """Dot-orbital density matrix and entropies after every step of a sweep (both
+    directions) against the oracle; chains ordered by m put orbitals of equal (species, m)
+    side by side, so the hopping element is exercised."""
+    from oracle.dmrg import OracleDMRG
+    from oracle.entropy import dot_rdm, entropies
+    prob = make_problem(space, Np, Nn, two_M, seed=seed)
+    if by_m:
+        prob = _by_m(prob)
+    init = initial_mps(prob, M0, seed + 100)
+    o = OracleDMRG(prob, init, tol=1e-10)
+    d = P.DMRG(prob, dav_tol=1e-10)
+    d.build_blocks(init)
+    with pytest.raises(P.DmrgError):
+        d.dot_rdm(1)                       # no wave function held yet
+    N = prob.n_sites
+    hop = 0.0
+    seq = [(p, "L") for p in range(1, N - 2)] + [(p, "R") for p in range(N - 3, 0, -1)]
+    for p, dr in seq:
+        o.run_step(p, dr, M)
+        d.step(p, 0 if dr == "L" else 1, M)
+        ref = dot_rdm(o.psi, o.psi_layout, o._prev_L, o._prev_R, o.ch.q[p], o.ch.q[p + 1])
+        rho, ent = d.dot_rdm(p)
+        assert np.max(np.abs(rho - ref)) < 1e-9, (p, dr, rho, ref)
+        assert np.max(np.abs(np.array(ent) - np.array(entropies(ref)))) < 1e-7, (p, dr)
+        hop = max(hop, abs(ref[1, 2]))
+    assert (hop > 1e-4) == by_m
