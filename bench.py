@@ -454,6 +454,21 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = heff_bytes / max(heff_s, 1e-12) / 1e9
     p_e2e, _ = seq[-1]
+    # dot-orbital density matrix of the last timed step's wave function (wall clock of the
+    # whole call: piece lists on the host, two kernels, read-back)
+    dot = None
+    try:
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, ent = d.dot_rdm(p_e2e)
+            ts.append(time.perf_counter() - t0)
+        size_last = d.psi_layout(p_e2e)["size"]
+        dot = {"position": p_e2e, "wall_ms": 1e3 * min(ts), "psi_elements": size_last,
+               "s_p": ent[0], "s_p1": ent[1], "I": ent[3]}
+    except Exception as exc:
+        dot = {"error": str(exc)}
     lay = d.psi_layout(p_e2e)
     # FP64 path on the same superblock: Davidson from the mixed eigenvector
     psi_m = torch.empty(lay["size"], dtype=torch.float64, device="cuda")
@@ -534,6 +549,7 @@ def run_gpu(args):
         "batch": batch,
         "precond": precond,
         "next_rows": next_rows,
+        "dot_rdm": dot,
         "e2e": e2e,
         "gpu_launches": int(c1["launches"] - c0["launches"]),
         "device_mem_used_gb": dev_used_gb,
