@@ -378,6 +378,22 @@ def run_next_rows(P, prob, init, M, e_fixed):
     return out
 
 
+def max_over_ranks(x, dist=None):
+    """The largest value of x over the ranks of the process group (x on a single rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, flops_per_rank, seconds_max):
+    """Whole-job TFLOP/s of `world` replicas: the work of every rank over the time of the
+    slowest one."""
+    return world * flops_per_rank / seconds_max / 1e12
+
+
 def run_gpu(args):
     import ctypes
     import numpy as np
@@ -442,15 +458,12 @@ def run_gpu(args):
     dev_used_gb = (total_b - free_b) / 1e9
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(timed))]
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, dist)
     flops = sum(s["heff_flops"] * s["n_products"] for s in stats)
     heff_s = sum(s["heff_seconds"] for s in stats)
     heff_bytes = sum(s["heff_bytes"] * s["n_products"] for s in stats)
     nprod = sum(s["n_products"] for s in stats)
-    value = world * flops / total_s / 1e12
+    value = replica_throughput(world, flops, total_s)
     peak, peak_kind = _peaks()
     achieved = heff_bytes / max(heff_s, 1e-12) / 1e9
     p_e2e, _ = seq[-1]
