@@ -23,6 +23,9 @@ Contents and pins (each checked by a ``-m "not gpu"`` test):
   two-orbital entropies.  Pinned by the exact ground state in the determinant basis
   (occupations, pair occupations, the hopping element with determinant signs) and by
   equal entropies of time-reversed orbitals.
+* ``ordering``: chain order from the mutual information (Fiedler vector of the graph
+  Laplacian).  Pinned by the path graph's closed form, recovery of a hidden chain, the
+  variational property, and brute force over all orders of a small case.
 * ``extrapolate``: least-squares E(M) fits.  Pinned by exact model data, the normal
   equations, an independent exponent scan and equivariance under shift and scale.
 """
