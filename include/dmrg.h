@@ -245,6 +245,20 @@ int dmrg_dot_rdm(dmrg_ctx* ctx, int32_t p, double* rho, double* ent);
  * trunc_target >= 1 or is NaN, or M_min < 1 with a positive target. */
 int dmrg_set_dbss(dmrg_ctx* ctx, int32_t M_min, double trunc_target);
 
+/* Orbital ordering from the two-orbital mutual information (host code, no context, no
+ * device work): the paper orders the orbitals so that the entanglement distance
+ * sum_ij I_ij |i - j|^2 is small, with spectral graph theory.  I: host n x n row-major
+ * symmetric matrix of non-negative weights (the diagonal is ignored), 2 <= n <= 1024.
+ * The graph Laplacian L = D - I is diagonalised (cyclic Jacobi, FP64); the eigenvector of
+ * its second smallest eigenvalue (the Fiedler vector, normalised, sign such that the
+ * lowest-index component within 1e-9 of the largest magnitude is positive) orders the
+ * orbitals: order[k] = the orbital placed at chain position k, by ascending component,
+ * equal components by index.  fiedler: optional host array of n for the vector.
+ * DMRG_EINVAL for bad sizes, a non-finite, asymmetric or negative weight, or a
+ * disconnected graph (second eigenvalue zero: no order between its parts).  When the
+ * second and third eigenvalues coincide the order is not unique.  Thread-safe. */
+int dmrg_fiedler_order(int32_t n, const double* I, int32_t* order, double* fiedler);
+
 /* Extrapolation of energies in the number of kept block states (host code, no context,
  * no device work).  Points (M[i], E[i]), i < n, are fitted by ordinary least squares:
  *   DMRG_FIT_POWER:     E(M) = E_inf + X1 M^X2, the truncation-free estimate of the

@@ -31,7 +31,7 @@ EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks
             "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
             "dmrg_mlp_params", "dmrg_mlp_loss_grad", "dmrg_mlp_n_params",
             "dmrg_batch_create", "dmrg_batch_destroy", "dmrg_batch_last_error",
-            "dmrg_batch_sweep", "dmrg_extrapolate"]
+            "dmrg_batch_sweep", "dmrg_extrapolate", "dmrg_fiedler_order"]
 PRECOND_DIAG = 0
 PRECOND_MLP = 1
 
@@ -140,6 +140,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_mlp_loss_grad": [P, i32, P, P, P, i64, P, P],
         "dmrg_get_counters": [P, ctypes.POINTER(Counters)],
         "dmrg_extrapolate": [i32, i32, P, P, P, P],
+        "dmrg_fiedler_order": [i32, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -176,6 +177,22 @@ def _np_ptr(a):
 
 FIT_POWER = 0
 FIT_QUADRATIC = 1
+
+
+def fiedler_order(I):
+    """Chain order of the orbitals from a symmetric mutual-information matrix (host code
+    in the library): (order, Fiedler vector), order[k] = orbital at chain position k."""
+    lib = load_library()
+    W = np.ascontiguousarray(I, dtype=np.float64)
+    if W.ndim != 2 or W.shape[0] != W.shape[1]:
+        raise ValueError("I must be a square matrix")
+    n = W.shape[0]
+    order = np.zeros(n, dtype=np.int32)
+    v = np.zeros(n)
+    rc = lib.dmrg_fiedler_order(int(n), _np_ptr(W), _np_ptr(order), _np_ptr(v))
+    if rc != DMRG_OK:
+        raise DmrgError(rc, "invalid or disconnected mutual-information matrix")
+    return [int(x) for x in order], v
 
 
 def extrapolate(M, E, kind=FIT_POWER):
