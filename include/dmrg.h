@@ -219,7 +219,8 @@ int dmrg_set_roots(dmrg_ctx* ctx, int32_t n_roots);
 /* Orbital entropies of the two dots (the one-orbital entropy s_i = -Tr rho_i ln rho_i and
  * the two-orbital mutual information of the paper's entanglement analysis) from the
  * wave function held for position p (after dmrg_davidson, dmrg_step or a sweep that ended
- * at p), on the device.  rho: optional host array of 16, the two-orbital reduced density
+ * at p; the lowest state when two are targeted), on the device.  rho: optional host array
+ * of 16, the two-orbital reduced density
  * matrix of chain positions p and p+1, row-major, basis index 2 n_p + n_{p+1} (|00>,
  * |01>, |10>, |11>), rho[a][b] = sum_{l,r} psi(l,a,r) psi(l,b,r); it is diagonal except
  * for the |01>,|10> element, which equals <c+_{p+1} c_p> and is nonzero only when the two
