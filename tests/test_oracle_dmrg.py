@@ -306,3 +306,39 @@ def test_two_state_sweeps_reach_the_two_lowest_exact_states(space, seed, M0):
     for _ in range(2):
         for r in t.sweep(4 if space == "p" else 16):
             assert r.energy >= e0 - 1e-10 and r.energy1 >= e1 - 1e-10
+
+
+# ---------------------------------------------------------------------------------------
+# the truncation's cut rules on wave functions with chosen weights
+# ---------------------------------------------------------------------------------------
+def _weights_psi(sb, weights):
+    """A wave function whose left density matrix has exactly the given eigenvalues: one
+    entry per chosen block (the blocks with the largest dims first), value sqrt(w)."""
+    x = np.zeros(sb.layout.size)
+    blocks = sorted(sb.layout.blocks, key=lambda b: -b[2] * b[3])
+    assert len(blocks) >= len(weights)
+    for (QL, QR, dL, dR, off), w in zip(blocks, weights):
+        x[off] = np.sqrt(w)
+    return x
+
+
+def test_cut_keeps_whole_multiplets_and_drops_zero_weights():
+    from oracle.dmrg import truncate
+    sb, _ = _psi_at(4)
+    # an exact pair at the cut is kept whole (M = 2 keeps 3)
+    x = _weights_psi(sb, [0.5, 0.25, 0.25])
+    _, keep, tr, _ = truncate(x, sb.layout, sb.L, "L", 2)
+    assert sum(keep.values()) == 3 and abs(tr) < 1e-15
+    # within the 1e-10 relative tolerance counts as degenerate, beyond it does not
+    x = _weights_psi(sb, [0.5, 0.25 * (1 + 2e-11), 0.25 * (1 - 2e-11)])
+    assert sum(truncate(x, sb.layout, sb.L, "L", 2)[1].values()) == 3
+    x = _weights_psi(sb, [0.5, 0.25 * (1 + 1e-8), 0.25 * (1 - 1e-8)])
+    _, keep, tr, _ = truncate(x, sb.layout, sb.L, "L", 2)
+    assert sum(keep.values()) == 2 and abs(tr - 0.25 * (1 - 1e-8)) < 1e-15
+    # weights at or below 1e-14 are never kept, even below M; all kept when D <= M
+    x = _weights_psi(sb, [1.0 - 2e-15, 1e-15, 1e-15])
+    D = sum(sb.L.dims.values())
+    _, keep, _, _ = truncate(x, sb.layout, sb.L, "L", D - 1)
+    assert sum(keep.values()) == 1
+    _, keep, _, _ = truncate(x, sb.layout, sb.L, "L", D)
+    assert keep == dict(sb.L.dims)
