@@ -342,3 +342,28 @@ def test_cut_keeps_whole_multiplets_and_drops_zero_weights():
     assert sum(keep.values()) == 1
     _, keep, _, _ = truncate(x, sb.layout, sb.L, "L", D)
     assert keep == dict(sb.L.dims)
+
+
+@pytest.mark.parametrize("Np,Nn,two_M", [(0, 3, 1), (0, 2, 0), (1, 0, 1), (6, 1, 1), (5, 5, 0),
+                                         (6, 6, 0)])
+def test_degenerate_particle_numbers(Np, Nn, two_M):
+    """One species absent, a single particle, a full proton shell, the completely filled
+    p shell (a one-state sector): complete bases reproduce exact diagonalization."""
+    p = make_problem("p", Np, Nn, two_M, seed=4)
+    e0 = ed_lowest(p)[0]
+    d = OracleDMRG(p, initial_mps(p, 6, 5))
+    d.sweep(10 ** 6)
+    res = d.sweep(10 ** 6)
+    assert abs(res[-1].energy - e0) < 1e-10
+
+
+def test_filled_shell_closed_form():
+    """Every orbital occupied: E = sum_i eps_i + sum_{i<j} vbar[ij, ij]."""
+    p = make_problem("p", 6, 6, 0, seed=4)
+    v = {tuple(k): x for k, x in zip(p.v_idx.tolist(), p.v_val.tolist())}
+    N = p.n_sites
+    e = float(np.sum(p.eps)) + sum(v.get((i, j, i, j), 0.0) for i in range(N)
+                                   for j in range(i + 1, N))
+    d = OracleDMRG(p, initial_mps(p, 6, 5))
+    res = d.sweep(10 ** 6)
+    assert abs(res[-1].energy - e) < 1e-10 and abs(ed_lowest(p)[0] - e) < 1e-10
