@@ -20,9 +20,10 @@ Contents and pins (each checked by a ``-m "not gpu"`` test):
   selection is pinned by brute force on singular values of the wave-function blocks,
   by its reductions to the fixed-M rule, and by the truncation bound along sweeps.
 * ``entropy``: two-orbital density matrix of the dot orbitals and the one- and
-  two-orbital entropies.  Pinned by the exact ground state in the determinant basis
-  (occupations, pair occupations, the hopping element with determinant signs) and by
-  equal entropies of time-reversed orbitals.
+  two-orbital entropies; every pair from the written-out state.  Pinned by the exact
+  ground state in the determinant basis (occupations, pair occupations, the hopping
+  element with determinant signs, for neighbours and across strings) and by equal
+  entropies of time-reversed orbitals.
 * ``ordering``: chain order from the mutual information (Fiedler vector of the graph
   Laplacian).  Pinned by the path graph's closed form, recovery of a hidden chain, the
   variational property, and brute force over all orders of a small case.

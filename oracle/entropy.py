@@ -9,9 +9,11 @@ two-orbital entropy s_ij.  Readings where the paper is silent or garbled:
 * the mutual information is I_ij = s_i + s_j - s_ij (non-negative; the printed formula
   has the opposite overall sign);
 * natural logarithms;
-* here only the two dot orbitals p, p+1 of a step are treated: their two-orbital density
-  matrix is read directly off the two-site wave function psi(l, n_p, n_{p+1}, r), so a
-  sweep yields s_i for every orbital and I_{p,p+1} for every neighbouring pair.
+* ``dot_rdm``: the two dot orbitals p, p+1 of a step, read directly off the two-site wave
+  function psi(l, n_p, n_{p+1}, r) (what the library computes);
+* ``state_amplitudes`` / ``pair_rdm`` / ``mutual_information``: every pair, from the
+  state written out in the occupation basis of the chain (small cases only; the plain
+  definition that a device implementation for all pairs will be checked against).
 
 Basis of the two-orbital matrix: index 2 n_p + n_{p+1} (|00>, |01>, |10>, |11>),
     rho[a, b] = sum_{l, r} psi(l, a, r) psi(l, b, r).
@@ -81,3 +83,103 @@ def entropies(rho):
     s_q = _vn([rho[0, 0] + rho[2, 2], rho[1, 1] + rho[3, 3]])
     s_pq = _vn(np.linalg.eigvalsh(rho))
     return s_p, s_q, s_pq, s_p + s_q - s_pq
+
+
+# ----------------------------------------------------------------------------------
+# every orbital pair, from the state written out in the occupation basis
+# ----------------------------------------------------------------------------------
+def _block_patterns(o):
+    """Left blocks (bonds 0..N-3) and right blocks (bonds 2..N-2) of an OracleDMRG as
+    {sector: (occupation bitmasks over chain positions, coefficients patterns x m)}."""
+    from .dmrg import enlarge_left, enlarge_right, vacuum
+    N = o.N
+    left, right = {}, {}
+    prev = {(0, 0, 0): ([0], np.ones((1, 1)))}
+    for b in range(0, N - 2):
+        if b not in o.UL:
+            break
+        blk = vacuum(1, 0) if b == 0 else o.left[b - 1]
+        enl = enlarge_left(blk, b, o.mpo, o.ch)
+        cur = {}
+        for Q, U in o.UL[b].items():
+            pats, E = _enlarged(enl.pieces[Q], prev, lambda pat, sg: pat | (sg << b), enl.dims[Q])
+            cur[Q] = (pats, E @ U)
+        left[b] = prev = cur
+    prev = {(0, 0, 0): ([0], np.ones((1, 1)))}
+    for b in range(N - 2, 1, -1):
+        if b not in o.UR:
+            break
+        blk = vacuum(1, 0) if b == N - 2 else o.right[b + 1]
+        enl = enlarge_right(blk, b + 1, o.mpo, o.ch)
+        cur = {}
+        for Q, U in o.UR[b].items():
+            pats, E = _enlarged(enl.pieces[Q], prev, lambda pat, sg: pat | (sg << (b + 1)),
+                                enl.dims[Q])
+            cur[Q] = (pats, E @ U)
+        right[b] = prev = cur
+    return left, right
+
+
+def _enlarged(pieces, blocks, place, D):
+    """Occupation-basis vectors of an enlarged sector's states: piece (sigma, q, off, d)
+    holds the d states of block sector q with the site in state sigma."""
+    pats, cols = [], []
+    for (sg, q, off, d) in pieces:
+        bp, C = blocks[q]
+        for k, pat in enumerate(bp):
+            pats.append(place(pat, sg))
+            row = np.zeros(D)
+            row[off:off + d] = C[k]
+            cols.append(row)
+    return pats, np.array(cols)
+
+
+def state_amplitudes(o):
+    """The wave function of the last step of an OracleDMRG written out: {occupation
+    bitmask over chain positions: amplitude} (tensor basis in chain order)."""
+    p = o.psi_at[0]
+    left, right = _block_patterns(o)
+    lb, rb = left[p - 1], right[p + 1]
+    Lenl, Renl = o._prev_L, o._prev_R
+    amp = {}
+    for (QL, QR, dL, dR, off) in o.psi_layout.blocks:
+        pl, EL = _enlarged(Lenl.pieces[QL], lb, lambda pat, sg: pat | (sg << p), dL)
+        pr, ER = _enlarged(Renl.pieces[QR], rb, lambda pat, sg: pat | (sg << (p + 1)), dR)
+        A = EL @ o.psi[off:off + dL * dR].reshape(dL, dR) @ ER.T
+        for i, a in enumerate(pl):
+            for j, c in enumerate(pr):
+                if A[i, j] != 0.0:
+                    amp[a | c] = amp.get(a | c, 0.0) + A[i, j]
+    return amp
+
+
+def pair_rdm(amp, i, j):
+    """Two-orbital density matrix of chain positions i < j from occupation amplitudes:
+    basis 2 n_i + n_j, off-diagonal element <c+_j c_i> (the Jordan-Wigner string gives
+    (-1)^(number of occupied positions strictly between i and j))."""
+    rho = np.zeros((4, 4))
+    x = 0.0
+    between = ((1 << j) - 1) & ~((1 << (i + 1)) - 1)
+    for pat, a in amp.items():
+        ni, nj = (pat >> i) & 1, (pat >> j) & 1
+        rho[2 * ni + nj, 2 * ni + nj] += a * a
+        if ni == 1 and nj == 0:
+            partner = amp.get((pat ^ (1 << i)) | (1 << j))
+            if partner is not None:
+                sign = -1.0 if bin(pat & between).count("1") & 1 else 1.0
+                x += sign * partner * a
+    rho[1, 2] = rho[2, 1] = x
+    return rho
+
+
+def mutual_information(amp, n):
+    """n x n matrix I_ij of the chain positions (zero diagonal) and the one-orbital
+    entropies s_i."""
+    I = np.zeros((n, n))
+    s = np.zeros(n)
+    for i in range(n):
+        for j in range(i + 1, n):
+            si, sj, _, mi = entropies(pair_rdm(amp, i, j))
+            I[i, j] = I[j, i] = mi
+            s[i], s[j] = si, sj
+    return I, s

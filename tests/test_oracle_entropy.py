@@ -107,3 +107,46 @@ def test_time_reversed_orbitals_have_equal_entropies():
             pairs += 1
     assert pairs >= prob.n_sites - 4
     assert max(s.values()) > 1e-3        # not a trivial (uncorrelated) state
+
+
+@pytest.mark.parametrize("Np,Nn,two_M,seed,by_m,string_hops",
+                         [(2, 2, 0, 12, False, False), (2, 1, 1, 3, False, True),
+                          (2, 1, 1, 3, True, False)])
+def test_every_pair_from_the_written_out_state(Np, Nn, two_M, seed, by_m, string_hops):
+    """The DMRG state written out in the occupation basis (chain order) gives the density
+    matrix of every orbital pair; at complete bases it equals the exact one, including the
+    hopping element across Jordan-Wigner strings of any length."""
+    from oracle.entropy import pair_rdm, state_amplitudes
+    prob = make_problem("p", Np, Nn, two_M, seed=seed)
+    if by_m:
+        prob = _ordered_by_m(prob)
+    basis, v, w, o = _exact_run(prob, 6)
+    amp = state_amplitudes(o)
+    assert abs(sum(a * a for a in amp.values()) - 1.0) < 1e-12
+    assert len(amp) == len(basis)
+    hop = 0.0
+    for i in range(o.N):
+        for j in range(i + 1, o.N):
+            ref = _rdm_from_determinants(basis, v, int(prob.order[i]), int(prob.order[j]))
+            assert np.max(np.abs(pair_rdm(amp, i, j) - ref)) < 1e-10, (i, j)
+            hop = max(hop, abs(ref[1, 2]) if j > i + 1 else 0.0)
+    # natural order: equal-m orbitals of different j lie apart, so a nonzero-J state hops
+    # across Jordan-Wigner strings; ordered by m they are neighbours
+    assert (hop > 1e-3) == string_hops
+
+
+def test_written_out_state_at_truncated_m():
+    """At truncated M the written-out state is normalised and its dot pair is the dot
+    density matrix read off the two-site wave function."""
+    from oracle.entropy import pair_rdm, state_amplitudes
+    prob = make_problem("p", 3, 3, 0, seed=5)
+    o = OracleDMRG(prob, initial_mps(prob, 4, 5), tol=1e-10)
+    o.sweep(4)
+    for p in range(1, 7):                 # steps in sweep order; checked at 3 and 6
+        o.run_step(p, "L", 4)
+        if p not in (3, 6):
+            continue
+        amp = state_amplitudes(o)
+        assert abs(sum(a * a for a in amp.values()) - 1.0) < 1e-12
+        ref = dot_rdm(o.psi, o.psi_layout, o._prev_L, o._prev_R, o.ch.q[p], o.ch.q[p + 1])
+        assert np.max(np.abs(pair_rdm(amp, p, p + 1) - ref)) < 1e-12

@@ -82,3 +82,23 @@ def test_rejected_inputs(P):
         with pytest.raises(P.DmrgError) as e:
             P.fiedler_order(I)
         assert e.value.code == P.DMRG_EINVAL
+
+
+def test_ordering_of_a_dmrg_state(P):
+    """The preprocessing chain on a small case: mutual information of every pair from a
+    DMRG state (oracle), ordered by the library; the order found shortens the
+    entanglement distance of the natural chain order."""
+    from gen import make_problem, initial_mps
+    from oracle.dmrg import OracleDMRG
+    from oracle.entropy import mutual_information, state_amplitudes
+    from oracle.ordering import entanglement_distance, fiedler_order, fiedler_vector
+    prob = make_problem("p", 3, 3, 0, seed=5)
+    o = OracleDMRG(prob, initial_mps(prob, 8, 5), tol=1e-10)
+    o.sweep(10 ** 6)
+    I, s = mutual_information(state_amplitudes(o), o.N)
+    order, vec = P.fiedler_order(I)
+    assert np.max(np.abs(vec - fiedler_vector(I))) < 1e-9
+    if _separated(fiedler_vector(I)):
+        assert order == fiedler_order(I)
+    d_nat = entanglement_distance(I, list(range(o.N)))
+    assert entanglement_distance(I, order) < 0.5 * d_nat
