@@ -367,3 +367,28 @@ def test_filled_shell_closed_form():
     d = OracleDMRG(p, initial_mps(p, 6, 5))
     res = d.sweep(10 ** 6)
     assert abs(res[-1].energy - e) < 1e-10 and abs(ed_lowest(p)[0] - e) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def sb_mid():
+    p = make_problem("sd", 2, 2, 0, seed=1)
+    d = OracleDMRG(p, initial_mps(p, 64, 5))
+    for q in range(1, 11):
+        d.run_step(q, "L", 64)
+    return d.superblock(11)
+
+
+@pytest.mark.parametrize("max_sub", [4, 7, 24])
+def test_davidson_with_restarts_finds_the_lowest_eigenpair(sb_mid, max_sub):
+    """A superblock of 169 states (sd 2p+2n, M = 64, mid-chain): Davidson with thick
+    restarts every max_sub vectors reaches the lowest eigenvalue of the dense H_eff."""
+    from oracle.dmrg import davidson
+    sb = sb_mid
+    n = sb.layout.size
+    assert n > 100
+    He = np.stack([sb.apply(np.eye(n)[:, c]) for c in range(n)], axis=1)
+    w = np.linalg.eigvalsh(He)
+    th, x, nprod, rn = davidson(sb.apply, sb.diagonal(), np.ones(n), tol=1e-9, max_iter=400,
+                                max_sub=max_sub)
+    assert rn <= 1e-9 and abs(th - w[0]) < 1e-10
+    assert np.linalg.norm(He @ x - th * x) < 1e-8
