@@ -38,7 +38,7 @@ extern "C" {
 #define DMRG_EINVAL (-1)    /* bad argument, inconsistent input, or call out of order */
 #define DMRG_ENOMEM (-2)    /* device or host allocation failed                       */
 #define DMRG_ECUDA (-3)     /* a CUDA call failed (message has the CUDA error string)  */
-#define DMRG_ENOCONV (-4)   /* Davidson hit dav_max_iter before the tolerance          */
+#define DMRG_ENOCONV (-4)   /* an iteration stopped at its limit (Davidson, Jacobi SVD) */
 #define DMRG_ETIMEOUT (-5)  /* a device-side wait gave up (bounded spin)               */
 
 #define DMRG_FP64 0         /* every contraction in FP64                               */
@@ -135,7 +135,9 @@ typedef struct {
    * allocation, [14] enlargement table uploads, [15] cudaMalloc calls (all contexts),
    * [16] Davidson: issuing the products, [17] Davidson: host work after each product,
    * [18] Davidson: waits after each product, [19] Davidson iterations (a count),
-   * [20..23] reserved */
+   * [20] truncation sectors too large for the cluster SVD, decomposed from the explicit
+   * density matrix instead (a count), [21] truncations whose SVD stopped at its sweep
+   * limit (a count), [22..23] reserved */
   double t_detail[24];
   int64_t pool_mallocs;     /* device allocations that missed the caching pool          */
   int64_t sb_small_tiles;   /* last superblock: tiles of the small-block product kernel */
@@ -192,7 +194,9 @@ int dmrg_davidson(dmrg_ctx* ctx, int32_t p, const double* guess_dev, double* psi
  * sector, FP64 eigendecomposition on the device, global selection of the M largest
  * weights (extended to the whole degenerate multiplet at the cut), and renormalization of
  * every normal and complementary operator of the new block.  trunc_err = discarded
- * weight; kept = number of kept states.  DMRG_EINVAL if no eigenvector is held for p. */
+ * weight; kept = number of kept states.  DMRG_EINVAL if no eigenvector is held for p;
+ * DMRG_ENOCONV if a density-matrix decomposition stopped at its sweep limit (the
+ * truncation and renormalization are still done). */
 int dmrg_truncate_renormalize(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t M,
                               double* trunc_err, int32_t* kept);
 
@@ -215,6 +219,26 @@ int dmrg_sweep(dmrg_ctx* ctx, int32_t M, dmrg_step_stats* steps, double* energy)
  * otherwise, here and in dmrg_set_options while two states are targeted); not available
  * in batch mode; a superblock with fewer than two states fails with DMRG_EINVAL. */
 int dmrg_set_roots(dmrg_ctx* ctx, int32_t n_roots);
+
+/* Eigenvalues and eigenvectors of the reduced density matrix of the wave function held for
+ * position p (after dmrg_davidson, dmrg_step or a sweep that ended at p), for every sector
+ * of the enlarged block on side dir (0: left, the block the left-to-right truncation keeps
+ * states of; 1: right) -- the decomposition behind the truncation's basis change by the
+ * SVD theorem, computed by the same kernels (the singular vectors of each wave-function
+ * block by one-sided Jacobi rotations, FP64); nothing is truncated or changed.  With two
+ * targeted states the matrix is the average of the two.
+ *   Call with NULL arrays to query n_sec and size (= sum of d^2); then qn [3 n_sec] (the
+ * sectors, ascending), dims [n_sec], w [sum of d] (each sector's eigenvalues, descending,
+ * clipped at 0), vecs [size] (optional: each sector's d x d row-major matrix whose columns
+ * are the eigenvectors in the order of w, each with its largest |component| positive, the
+ * lowest row on ties; the columns of zero eigenvalues may be zero).
+ *   cluster: 0 = work split chosen per sector; 1, 8 or 16 = every sector whose shared-memory
+ * share fits is decomposed by thread-block clusters of that many CTAs (the result is the
+ * same up to rounding; this checks the partitioning).
+ *   DMRG_EINVAL without a held wave function or for bad arguments; DMRG_ENOCONV if an SVD
+ * stopped at its sweep limit (the results are still returned). */
+int dmrg_rdm_eigh(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t cluster, int32_t* n_sec,
+                  int64_t* size, int32_t* qn, int32_t* dims, double* w, double* vecs);
 
 /* Orbital entropies of the two dots (the one-orbital entropy s_i = -Tr rho_i ln rho_i and
  * the two-orbital mutual information of the paper's entanglement analysis) from the

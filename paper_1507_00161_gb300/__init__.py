@@ -25,6 +25,7 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
+            "dmrg_rdm_eigh",
             "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_dot_rdm",
             "dmrg_get_counters",
             "dmrg_heff_cost",
@@ -133,6 +134,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_set_dbss": [P, i32, dbl],
         "dmrg_set_roots": [P, i32],
         "dmrg_dot_rdm": [P, i32, P, P],
+        "dmrg_rdm_eigh": [P, i32, i32, i32, P, P, P, P, P, P],
         "dmrg_mlp_reset": [P, ctypes.c_uint64],
         "dmrg_mlp_harvest": [P, i32, i32],
         "dmrg_mlp_train": [P, i32, i32, dbl, ctypes.c_uint64, P, P],
@@ -270,6 +272,33 @@ class DMRG:
         ent = np.zeros(4)
         self._check(self.lib.dmrg_dot_rdm(self.h, int(p), _np_ptr(rho), _np_ptr(ent)))
         return rho.reshape(4, 4), tuple(float(x) for x in ent)
+
+    def rdm_eigh(self, p, direction, cluster=0, vectors=True):
+        """Per-sector spectrum (and eigenvectors) of the reduced density matrix of the wave
+        function held for p on side `direction`: a list of (qn, w, V) with w descending and
+        V (d x d) holding the eigenvectors as columns (None when vectors=False)."""
+        n = ctypes.c_int32()
+        size = ctypes.c_int64()
+        self._check(self.lib.dmrg_rdm_eigh(self.h, int(p), int(direction), int(cluster),
+                                           ctypes.byref(n), ctypes.byref(size), None, None,
+                                           None, None))
+        qn = np.zeros((n.value, 3), dtype=np.int32)
+        dims = np.zeros(n.value, dtype=np.int32)
+        self._check(self.lib.dmrg_rdm_eigh(self.h, int(p), int(direction), int(cluster), None,
+                                           None, _np_ptr(qn), _np_ptr(dims), None, None))
+        w = np.zeros(int(dims.sum()))
+        vecs = np.zeros(size.value) if vectors else np.zeros(0)
+        self._check(self.lib.dmrg_rdm_eigh(self.h, int(p), int(direction), int(cluster), None,
+                                           None, _np_ptr(qn), _np_ptr(dims), _np_ptr(w),
+                                           _np_ptr(vecs) if vectors else None))
+        out, wo, vo = [], 0, 0
+        for i in range(n.value):
+            d = int(dims[i])
+            V = vecs[vo:vo + d * d].reshape(d, d).copy() if vectors else None
+            out.append((tuple(int(x) for x in qn[i]), w[wo:wo + d].copy(), V))
+            wo += d
+            vo += d * d
+        return out
 
     def set_dbss(self, m_min, trunc_target):
         """Dynamic block state selection: M passed to the truncating calls becomes the

@@ -358,6 +358,25 @@ void batched_eigh2(const int64_t* d_off, const int64_t* d_woff, const int32_t* d
                    cudaStream_t s);
 void ritz_solve(const double* d_H, int ld, int k, double* d_scratch, double* d_w, double* d_Y,
                 cudaStream_t s);
+// eigenpairs of rho_Q = B B^T from the singular vectors of the wave-function block B
+// (svd.cu): B = psi block (d x e, trans 0) or its transpose (trans 1, the block is e x d),
+// [psi0 psi1] / sqrt(2) with two roots; eigenvalues descending at w_off, eigenvectors as
+// the columns of a d x d row-major matrix at vs_off (largest |component| positive)
+struct SvdJob {
+  int64_t src;      // offset of the block in psi0 (and psi1)
+  int64_t vs_off;   // output eigenvectors
+  int64_t w_off;    // output eigenvalues
+  int32_t D;        // sector dimension d
+  int32_t e;        // the block's other dimension
+  int32_t trans;
+  int32_t roots;
+};
+size_t svd_smem_bytes(const SvdJob& j, int cluster);
+size_t svd_smem_limit();   // largest dynamic shared memory of one CTA of the SVD kernel
+// one cluster of `cluster` CTAs (1, 8 or 16) per job; *d_noconv = 1 if a job reached its
+// sweep limit
+void svd_jacobi(const SvdJob* d_jobs, int n_jobs, int cluster, size_t smem, const double* psi0,
+                const double* psi1, double* w, double* vs, int* d_noconv, cudaStream_t s);
 // a piece of a wave-function block paired with another (or itself): the sum over
 // i < nr, j < nc of psi[a + i lda + j] psi[b + i ldb + j] goes to sum number slot (0..4)
 struct RdmTask {

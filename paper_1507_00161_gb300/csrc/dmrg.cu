@@ -224,6 +224,8 @@ struct dmrg_ctx {
   std::unique_ptr<dmrg::Super> prev;   // layouts of the superblock psi belongs to
   // scratch
   dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
+  dmrg::DevBuf<int> noconv;    // set by a truncation SVD that reached its sweep limit
+  int64_t eig_noconv = 0;      // truncations with such an SVD
   dmrg::DevBuf<float> f32a, f32b, f32T, part32;
   dmrg::DevBuf<double> part64, xpad64, ybat64;
   dmrg::DevBuf<float> xpad32;
@@ -1757,69 +1759,123 @@ static DavResult davidson(Ctx& c, Super& sb, const double* guess, double* out,
 struct TruncResult {
   double trunc = 0.0;
   int kept = 0;
+  bool noconv = false;   // a Jacobi SVD stopped at its sweep limit (result still installed)
 };
 
-static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
-  wait_prefetch(c);   // a plan being made reads stored blocks; this changes one
-  PhaseTimer tm(c.t_truncate);
-  DMRG_REQUIRE(c.sb && c.sb->p == p && c.psi_valid && c.psi_p == p, DMRG_EINVAL,
-               "no eigenvector held for this position (call dmrg_davidson first)");
-  DMRG_REQUIRE(c.n_roots == 1 || c.psi1_valid, DMRG_EINVAL,
-               "no second targeted state held for this position");
-  DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
-  DMRG_REQUIRE(M >= 1, DMRG_EINVAL, "M must be positive");
-  Super& sb = *c.sb;
-  cudaStream_t s = c.stream;
-  const Layout& lay = dir == 0 ? sb.Ll : sb.Rl;
-  const int ns = lay.sec.size();
+// Eigenpairs of the reduced density matrix of every sector of the truncated side (dir 0:
+// enlarged left, dir 1: enlarged right) of the wave function held for the current
+// superblock: eigenvalues descending into c.ew (at woff), eigenvectors as the columns of
+// d x d row-major matrices into c.eVs (at roff), from the singular vectors of the
+// wave-function blocks (svd.cu); sectors too large for a cluster's shared memory fall back
+// to the two-sided Jacobi of the explicit density matrix (kernels.cu).  force_cluster
+// (1, 8, 16) sends every sector whose shared memory fits to clusters of that size (0:
+// chosen by the work of the sector).  Returns true if an SVD reached its sweep limit.
+struct RdmLayout {
+  int ns = 0;
   int64_t total = 0, sq = 0;
-  std::vector<int64_t> roff(ns), woff(ns);
-  std::vector<int32_t> dims(ns);
-  for (int i = 0; i < ns; ++i) {
-    roff[i] = sq;
-    woff[i] = total;
-    dims[i] = lay.sec.d[i];
-    sq += int64_t(lay.sec.d[i]) * lay.sec.d[i];
-    total += lay.sec.d[i];
+  std::vector<int64_t> roff, woff;
+  std::vector<int32_t> dims;
+};
+
+static RdmLayout rdm_layout(const Layout& lay) {
+  RdmLayout r;
+  r.ns = lay.sec.size();
+  r.roff.resize(r.ns);
+  r.woff.resize(r.ns);
+  r.dims.resize(r.ns);
+  for (int i = 0; i < r.ns; ++i) {
+    r.roff[i] = r.sq;
+    r.woff[i] = r.total;
+    r.dims[i] = lay.sec.d[i];
+    r.sq += int64_t(lay.sec.d[i]) * lay.sec.d[i];
+    r.total += lay.sec.d[i];
   }
-  // dynamic block state selection: M is the ceiling, dbss_min the floor
-  const bool dbss = c.dbss_target > 0.0;
-  const int floor_m = dbss ? std::min(c.dbss_min, M) : M;
-  Iso iso;
-  TruncResult tr;
-  if (total <= floor_m) {
-    launch_rq(c);
-    identity_iso(c, lay, iso);
-    tr.trunc = 0.0;
-    tr.kept = int(total);
-  } else {
-    // rho = psi psi^T per sector, or the average over the two targeted states
-    const bool two = c.n_roots == 2;
+  return r;
+}
+
+static bool rdm_eigh(Ctx& c, Super& sb, int dir, const RdmLayout& L, int force_cluster) {
+  cudaStream_t s = c.stream;
+  const int ns = L.ns;
+  const int64_t total = L.total, sq = L.sq;
+  const std::vector<int64_t>& roff = L.roff;
+  const std::vector<int64_t>& woff = L.woff;
+  const std::vector<int32_t>& dims = L.dims;
+  // eigenpairs of rho_Q = B B^T per sector from the singular vectors of the wave-function
+  // block B (svd.cu); sectors too large for a cluster's shared memory fall back to the
+  // two-sided Jacobi of the explicit rho (kernels.cu)
+  const bool two = c.n_roots == 2;
+  const int roots = two ? 2 : 1;
+  c.eVs.alloc(sq);
+  c.ew.alloc(total);
+  c.noconv.alloc(1);
+  DMRG_CUDA(cudaMemsetAsync(c.eVs.p, 0, sizeof(double) * sq, s));
+  DMRG_CUDA(cudaMemsetAsync(c.ew.p, 0, sizeof(double) * total, s));
+  DMRG_CUDA(cudaMemsetAsync(c.noconv.p, 0, sizeof(int), s));
+  std::vector<SvdJob> jobs[3];            // clusters of 1, 8 and 16 CTAs
+  size_t smem[3] = {0, 0, 0};
+  const int csize[3] = {1, 8, 16};
+  std::vector<int> fallback;              // sector indices for the explicit-rho path
+  for (int Q = 0; Q < ns; ++Q) {
+    const int b = dir == 0 ? sb.psi_of_L[Q] : sb.psi_of_R[Q];
+    if (b < 0) continue;                  // no wave-function block: rho_Q = 0
+    SvdJob j;
+    j.src = sb.boff[b];
+    j.vs_off = roff[Q];
+    j.w_off = woff[Q];
+    j.D = dims[Q];
+    j.e = dir == 0 ? sb.bdr[b] : sb.bdl[b];
+    j.trans = dir;
+    j.roots = roots;
+    DMRG_REQUIRE(j.D == (dir == 0 ? sb.bdl[b] : sb.bdr[b]), DMRG_EINVAL,
+                 "internal: wave-function block does not match its sector");
+    const double d = j.D, E = double(j.e) * roots;
+    const double cols = std::min(d, E), rows = std::max(d, E);
+    const double work = cols * cols * (rows + (d < E ? d : 0.0));
+    int cls = work < 4.0e5 ? 0 : (work < 8.0e6 ? 1 : 2);
+    if (force_cluster) cls = force_cluster == 1 ? 0 : force_cluster == 8 ? 1 : 2;
+    while (cls < 3 && svd_smem_bytes(j, csize[cls]) > svd_smem_limit()) ++cls;
+    if (cls == 3) {
+      fallback.push_back(Q);
+      continue;
+    }
+    jobs[cls].push_back(j);
+    smem[cls] = std::max(smem[cls], svd_smem_bytes(j, csize[cls]));
+  }
+  DevBuf<SvdJob> djobs[3];
+  for (int k = 0; k < 3; ++k) {
+    if (jobs[k].empty()) continue;
+    djobs[k].upload(jobs[k], s);
+    svd_jacobi(djobs[k].p, int(jobs[k].size()), csize[k], smem[k], c.psi.p,
+               two ? c.psi1.p : c.psi.p, c.ew.p, c.eVs.p, c.noconv.p, s);
+  }
+  c.t_detail[20] += double(fallback.size());
+  if (!fallback.empty()) {
+    // rho = psi psi^T (or the average over the two targeted states) for these sectors
     const double wgt = two ? 0.5 : 1.0;
     TaskList R;
-    for (size_t b = 0; b < sb.bL.size(); ++b) {
+    std::vector<int64_t> foff, fwoff;
+    std::vector<int32_t> fdim;
+    for (int Q : fallback) {
+      const int b = dir == 0 ? sb.psi_of_L[Q] : sb.psi_of_R[Q];
       const int dL = sb.bdl[b], dR = sb.bdr[b];
+      DMRG_REQUIRE(dims[Q] <= 1024, DMRG_EINVAL, "sector dimension above 1024 not supported");
       if (dir == 0) {
-        const int Q = sb.bL[b];
         R.begin_task(Operand{roff[Q], B_Y, dL}, dL, dL);
         R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dR, 2, wgt);
         if (two)
           R.add_term(Operand{sb.boff[b], B_Z, dR}, Operand{sb.boff[b], B_Z, dR}, dR, 2, wgt);
       } else {
-        const int Q = sb.bR[b];
         R.begin_task(Operand{roff[Q], B_Y, dR}, dR, dR);
         R.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dL, 1, wgt);
         if (two)
           R.add_term(Operand{sb.boff[b], B_Z, dR}, Operand{sb.boff[b], B_Z, dR}, dL, 1, wgt);
       }
+      foff.push_back(roff[Q]);
+      fwoff.push_back(woff[Q]);
+      fdim.push_back(dims[Q]);
     }
     c.rho.alloc(sq);
     c.eV.alloc(sq);
-    c.eVs.alloc(sq);
-    c.ew.alloc(total);
-    int64_t np2 = 1;
-    while (np2 < total) np2 <<= 1;
-    c.sel.alloc(np2 + 4 * int64_t(ns) + 16);
     DMRG_CUDA(cudaMemsetAsync(c.rho.p, 0, sizeof(double) * sq, s));
     DevTaskList dR;
     {
@@ -1834,15 +1890,63 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     bb.p[B_Y] = c.rho.p;
     if (two) bb.p[B_Z] = c.psi1.p;
     run_gemm_tasks<double>(dR, bb, 1, s);
-    int maxd = 0;
-    for (int x : dims) maxd = std::max(maxd, x);
-    DMRG_REQUIRE(maxd <= 1024, DMRG_EINVAL, "sector dimension above 1024 not supported");
+    DevBuf<int64_t> dfo, dfw;
+    DevBuf<int32_t> dfd;
+    dfo.upload(foff, s);
+    dfw.upload(fwoff, s);
+    dfd.upload(fdim, s);
+    batched_eigh2(dfo.p, dfw.p, dfd.p, int(fallback.size()), c.rho.p, c.eV.p, c.eVs.p, c.ew.p,
+                  1, 1, s);
+    sync(c);   // the uploaded tables live until here
+  }
+  int noconv = 0;
+  DMRG_CUDA(cudaMemcpyAsync(&noconv, c.noconv.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  sync(c);   // the job tables live until here
+  return noconv != 0;
+}
+
+static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
+  wait_prefetch(c);   // a plan being made reads stored blocks; this changes one
+  PhaseTimer tm(c.t_truncate);
+  DMRG_REQUIRE(c.sb && c.sb->p == p && c.psi_valid && c.psi_p == p, DMRG_EINVAL,
+               "no eigenvector held for this position (call dmrg_davidson first)");
+  DMRG_REQUIRE(c.n_roots == 1 || c.psi1_valid, DMRG_EINVAL,
+               "no second targeted state held for this position");
+  DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
+  DMRG_REQUIRE(M >= 1, DMRG_EINVAL, "M must be positive");
+  Super& sb = *c.sb;
+  cudaStream_t s = c.stream;
+  const Layout& lay = dir == 0 ? sb.Ll : sb.Rl;
+  const RdmLayout RL = rdm_layout(lay);
+  const int ns = RL.ns;
+  const int64_t total = RL.total;
+  const std::vector<int64_t>& roff = RL.roff;
+  const std::vector<int64_t>& woff = RL.woff;
+  const std::vector<int32_t>& dims = RL.dims;
+  // dynamic block state selection: M is the ceiling, dbss_min the floor
+  const bool dbss = c.dbss_target > 0.0;
+  const int floor_m = dbss ? std::min(c.dbss_min, M) : M;
+  Iso iso;
+  TruncResult tr;
+  if (total <= floor_m) {
+    launch_rq(c);
+    identity_iso(c, lay, iso);
+    tr.trunc = 0.0;
+    tr.kept = int(total);
+  } else {
+    const bool noconv = rdm_eigh(c, sb, dir, RL, 0);
+    if (noconv) {
+      tr.noconv = true;
+      c.eig_noconv += 1;
+    }
+    int64_t np2 = 1;
+    while (np2 < total) np2 <<= 1;
+    c.sel.alloc(np2 + 4 * int64_t(ns) + 16);
     DevBuf<int64_t> droff, dwoff, duoff;
     DevBuf<int32_t> ddim, dkept;
     droff.upload(roff, s);
     dwoff.upload(woff, s);
     ddim.upload(dims, s);
-    batched_eigh2(droff.p, dwoff.p, ddim.p, ns, c.rho.p, c.eV.p, c.eVs.p, c.ew.p, 1, 1, s);
     double* lamM = c.sel.p + np2;
     double* kw = lamM + 8;
     kth_largest(c.ew.p, total, std::min<int64_t>(M, total), floor_m, dbss ? c.dbss_target : 0.0,
@@ -2386,6 +2490,49 @@ extern "C" int dmrg_truncate_renormalize(dmrg_ctx* c, int32_t p, int32_t dir, in
     TruncResult tr = truncate_renormalize(*c, p, dir, M);
     if (trunc_err) *trunc_err = tr.trunc;
     if (kept) *kept = tr.kept;
+    DMRG_REQUIRE(!tr.noconv, DMRG_ENOCONV,
+                 "a density-matrix eigendecomposition stopped at its sweep limit (result "
+                 "installed)");
+  });
+}
+
+extern "C" int dmrg_rdm_eigh(dmrg_ctx* c, int32_t p, int32_t dir, int32_t cluster,
+                             int32_t* n_sec, int64_t* size, int32_t* qn, int32_t* dims,
+                             double* w, double* vecs) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(c->psi_valid && c->psi_p == p, DMRG_EINVAL,
+                 "no wave function held for this position (run dmrg_davidson or dmrg_step)");
+    DMRG_REQUIRE(dir == 0 || dir == 1, DMRG_EINVAL, "dir must be 0 or 1");
+    DMRG_REQUIRE(cluster == 0 || cluster == 1 || cluster == 8 || cluster == 16, DMRG_EINVAL,
+                 "cluster must be 0, 1, 8 or 16");
+    DMRG_REQUIRE(c->n_roots == 1 || c->psi1_valid, DMRG_EINVAL,
+                 "no second targeted state held for this position");
+    Super* sb = (c->sb && c->sb->p == p) ? c->sb.get()
+                                          : (c->prev && c->prev->p == p ? c->prev.get() : nullptr);
+    DMRG_REQUIRE(sb != nullptr, DMRG_EINVAL, "the layout of the held wave function is gone");
+    const Layout& lay = dir == 0 ? sb->Ll : sb->Rl;
+    const RdmLayout RL = rdm_layout(lay);
+    if (n_sec) *n_sec = RL.ns;
+    if (size) *size = RL.sq;
+    if (!qn && !dims && !w && !vecs) return;
+    const bool noconv = rdm_eigh(*c, *sb, dir, RL, cluster);
+    for (int i = 0; i < RL.ns; ++i) {
+      if (qn) {
+        qn[3 * i] = lay.sec.q[i].a;
+        qn[3 * i + 1] = lay.sec.q[i].b;
+        qn[3 * i + 2] = lay.sec.q[i].m;
+      }
+      if (dims) dims[i] = RL.dims[i];
+    }
+    if (w && RL.total)
+      DMRG_CUDA(cudaMemcpyAsync(w, c->ew.p, sizeof(double) * RL.total, cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (vecs && RL.sq)
+      DMRG_CUDA(cudaMemcpyAsync(vecs, c->eVs.p, sizeof(double) * RL.sq, cudaMemcpyDeviceToHost,
+                                c->stream));
+    sync(*c);
+    DMRG_REQUIRE(!noconv, DMRG_ENOCONV,
+                 "a density-matrix eigendecomposition stopped at its sweep limit");
   });
 }
 
@@ -2588,6 +2735,7 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     out->sb_kernel_flops = c->kernel_flops;
     for (int i = 0; i < 24; ++i) out->t_detail[i] = c->t_detail[i];
     out->t_detail[15] = 1e-9 * double(g_malloc_ns.load());
+    out->t_detail[21] = double(c->eig_noconv);
     out->pool_mallocs = g_malloc_count.load();
   });
 }
