@@ -1,22 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 DMRG hot path.
 
-Workload: pf shell, 40 m-scheme sites, 8 protons + 8 neutrons, M_z = 0 (m-scheme
-dimension 1,087,455,228), J-coupled random two-body ensemble (sigma = 1 MeV, seed 3),
-single-particle energies U[0,4) MeV, M = 4096 block states.  Setup (untimed): starting
-state with M = 4096 per right block, block build, two-site steps from position 1 to the
-middle of the chain.  A timed step is one full two-site DMRG step at the middle of the
-chain (superblock operators, Davidson with H_eff products, reduced-density-matrix
-truncation, renormalization of every normal and complementary operator) in the mixed
-path (FP32 operator contractions, FP64 Davidson / eigensolver / energy).
+Workload (the headline configuration): pf shell, 40 m-scheme sites, 8 protons + 8 neutrons,
+M_z = 0 (m-scheme dimension 1,087,455,228), J-coupled random two-body ensemble (sigma = 1
+MeV, seed 3), single-particle energies U[0,4) MeV; seeded random starting state (seed
+3003); M schedule 512(2) -> 1024(2) -> 2048(2) -> 4096(4) sweeps.
 
-Reported: value = H_eff psi TFLOP/s over the timed steps (algorithmic flops of every
-H_eff product / device time of the whole steps, CUDA events), the H_eff products' own
-device time and their HBM roofline, the FP64 path on the same superblock and the energy
-difference between the two, e2e = the same metric over a whole job through the public API
-(fresh context from host arrays, block build, one sweep at M = 4096 from the starting
-state, energy read back; wall clock), sweep_s = that sweep's seconds, a batch of 32
-small instances looped vs batched, and the FP64 CPU oracle as the CPU baseline.
+* e2e: the whole schedule as one job through the public API: a context created from the
+  host arrays of the Hamiltonian, the blocks built from the host starting state, ten
+  sweeps, every sweep's step records and energy read back; H_eff TFLOP/s over the job's
+  wall clock.  The sweeps at M = 4096 give sweep_s (median, CUDA events).
+* value: H_eff TFLOP/s over K two-site steps at M = 4096 after the schedule (left to
+  right, centred on the middle of the chain, after W warm-up steps): algorithmic flops of
+  every H_eff product / device time of the whole steps (superblock operators, Davidson,
+  truncation by the density-matrix SVDs, renormalization of every normal and complementary
+  operator), mixed path: FP32 operator contractions on split-TF32 tensor cores, FP64
+  Davidson vectors, SVDs and energies.
+* roofline: the H_eff product's algorithmic bytes / its device time (CUDA events around
+  every product) against the measured copy bandwidth.
+* fp64: mixed vs FP64 Davidson on the identical superblock of the heaviest timed position
+  (the energy gate), and one FP64 sweep at M = 4096 from the state the schedule reached.
+* cpu_baseline: the FP64 oracle's H_eff products on the same workload (position 1), timed
+  on the host cores in a child process.
+Side measurements (the schedule's sweeps, the timed steps, batch mode, the learned
+preconditioner, the next rows) are printed on lines of their own before the final line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -35,12 +42,11 @@ sys.path.insert(0, ROOT)
 METRIC = "H_eff·ψ TFLOP/s + sweep s at M=4096, mixed vs FP64 GPU at |ΔE|≤1e-5 MeV"
 WORKLOAD = dict(space="pf", Np=8, Nn=8, two_Mz=0, seed=3, mps_seed=3003, M=4096)
 WORKLOAD_NAME = ("pf-shell 40 sites, 8p+8n, M_z=0 (m-scheme dim 1,087,455,228), random "
-                 "J-coupled TBME sigma=1 MeV seed 3, M=4096, mid-chain two-site steps")
-# DRAM bytes (read + write) per mixed H_eff product of the default workload, from the one-pass
-# ncu capture of the timed steps in profiles/step_kernels_pf8p8n_M4096.md (sum over the
-# product's kernels / products); to be re-taken whenever those kernels change
-HEFF_TRAFFIC_BYTES = 175.3e6
-CPU_SAMPLE = dict(space="sd", Np=2, Nn=2, two_Mz=0, seed=1, mps_seed=5, M=64)
+                 "J-coupled TBME sigma=1 MeV seed 3, schedule 512(2)->1024(2)->2048(2)->"
+                 "4096(4), then two-site steps at M=4096 centred on the middle of the chain")
+# the oracle's sample of the same workload: its H_eff products at position 1 with the
+# starting state's right blocks at M0 states (building those blocks is not timed)
+CPU_SAMPLE_M0 = 512
 
 
 def _peaks():
@@ -133,53 +139,39 @@ def _oracle_heff_flops(sb):
     return f
 
 
-def cpu_oracle_sample(steps, warmup, budget_s=25.0):
-    """Times the oracle's H_eff products during two-site steps of the sd 2p+2n, M=64
-    workload (FP64 numpy).  Returns (TFLOP/s, seconds, products, description)."""
+def cpu_oracle_sample(steps, warmup, budget_s=20.0, M0=None):
+    """Times the oracle's H_eff products (FP64 numpy) on the headline workload: the
+    superblock at position 1 with the starting state's right blocks at M0 states (building
+    them is not timed), a seeded random input, repeated until the budget is spent.
+    Returns (TFLOP/s, seconds, products, description)."""
+    import numpy as np
     from gen import make_problem, initial_mps
     from oracle.dmrg import OracleDMRG
-    w = CPU_SAMPLE
+    w = WORKLOAD
+    M0 = CPU_SAMPLE_M0 if M0 is None else M0
     prob = make_problem(w["space"], w["Np"], w["Nn"], w["two_Mz"], seed=w["seed"])
-    o = OracleDMRG(prob, initial_mps(prob, w["M"], w["mps_seed"]))
-    # instrument the oracle's superblock product (timing only; arithmetic untouched)
-    stats = {"flops": 0.0, "t": 0.0, "n": 0}
-    orig = o.superblock
-
-    def timed_superblock(p):
-        sb = orig(p)
-        fl = _oracle_heff_flops(sb)
-        app = sb.apply
-
-        def apply(x):
-            t0 = time.perf_counter()
-            y = app(x)
-            stats["t"] += time.perf_counter() - t0
-            stats["flops"] += fl
-            stats["n"] += 1
-            return y
-        sb.apply = apply
-        return sb
-    o.superblock = timed_superblock
-    N = prob.n_sites
-    mid = N // 2 - 1
-    t_start = time.perf_counter()
-    for p in range(1, mid):
-        o.run_step(p, "L", w["M"])
-    stats.update(flops=0.0, t=0.0, n=0)
-    done = 0
-    for p in range(mid, N - 2):
-        if done >= warmup + steps or time.perf_counter() - t_start > budget_s:
+    t_setup = time.perf_counter()
+    o = OracleDMRG(prob, initial_mps(prob, M0, w["mps_seed"]))
+    sb = o.superblock(1)
+    t_setup = time.perf_counter() - t_setup
+    fl = _oracle_heff_flops(sb)
+    x = np.random.default_rng(1).standard_normal(sb.layout.size)
+    for _ in range(max(1, warmup)):
+        sb.apply(x)
+    n, t = 0, 0.0
+    while n < max(1, steps) or t < min(budget_s, 2.0):
+        t0 = time.perf_counter()
+        sb.apply(x)
+        t += time.perf_counter() - t0
+        n += 1
+        if t > budget_s:
             break
-        if done == warmup:
-            stats.update(flops=0.0, t=0.0, n=0)
-        o.run_step(p, "L", w["M"])
-        done += 1
-    tf = stats["flops"] / max(stats["t"], 1e-12) / 1e12
-    desc = (f"oracle H_eff products in {max(done - warmup, 0)} mid-chain two-site steps of sd "
-            f"2p+2n (m-scheme dim 640), M=64, FP64 numpy; {stats['n']} products, "
-            f"{stats['t']:.2f} s (the pf 8p+8n environment takes the plain oracle ~200 s to "
-            f"build)")
-    return tf, stats["t"], stats["n"], desc
+    tf = fl * n / max(t, 1e-12) / 1e12
+    desc = ("oracle H_eff products of pf 8p+8n (the headline workload) at position 1, "
+            "starting-state right blocks of M0=%d states (built in %.0f s, untimed); "
+            "psi of %d elements, %.3g GFLOP per product; %d products in %.2f s, FP64 numpy"
+            % (M0, t_setup, sb.layout.size, fl / 1e9, n, t))
+    return tf, t, n, desc
 
 
 def run_reference(args):
@@ -187,13 +179,17 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"          # before numpy loads: the oracle on one core
     t0 = time.perf_counter()
-    tf, secs, nprod, desc = cpu_oracle_sample(args.steps, args.warmup, budget_s=240.0)
+    tf, secs, nprod, desc = cpu_oracle_sample(args.steps, args.warmup, budget_s=60.0)
     line = {"impl": "reference", "metric": METRIC, "value": tf, "unit": "TFLOP/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": nprod, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(nprod, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample": desc},
+            "config": {"workload": WORKLOAD_NAME, "sample": desc,
+                       "step": "one oracle H_eff product (a whole two-site step of the oracle "
+                               "at this size takes hours)"},
             "cpu_baseline": {"value": tf, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": tf, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -394,6 +390,25 @@ def replica_throughput(world, flops_per_rank, seconds_max):
     return world * flops_per_rank / seconds_max / 1e12
 
 
+SCHEDULE = [(512, 2), (1024, 2), (2048, 2), (4096, 4)]
+
+
+def _timed_window(N, steps, warmup):
+    """(setup, warm-up, timed) positions of a left-to-right pass whose timed steps are
+    centred on the middle of the chain."""
+    start = max(1, min(N - 2 - steps, N // 2 - 1 - steps // 2))
+    w0 = max(1, start - warmup)
+    warm = [(p, 0) for p in range(w0, start)]
+    setup = [(p, 0) for p in range(1, w0)]
+    timed = [(p, 0) for p in range(start, min(N - 2, start + steps))]
+    return setup, warm, timed
+
+
+def _emit(tag, obj):
+    """A side measurement on a line of its own (the final line carries the headline)."""
+    print(json.dumps({"bench_section": tag, **obj}), flush=True)
+
+
 def run_gpu(args):
     import ctypes
     import numpy as np
@@ -415,30 +430,60 @@ def run_gpu(args):
     from gen import make_problem, initial_mps
     w = dict(WORKLOAD)
     wname = WORKLOAD_NAME
+    schedule = list(SCHEDULE)
     if args.workload:
         # another system of the same family (profiling of smaller cases)
         sp, npr, nne, sd = args.workload.split(":")
         w.update(space=sp, Np=int(npr), Nn=int(nne), seed=int(sd), two_Mz=(int(npr) + int(nne)) % 2)
-        wname = "%s shell, %dp+%dn, seed %d, M=%d (profiling case)" % (sp, int(npr), int(nne),
-                                                                       int(sd), args.M)
-    M = args.M
+        wname = "%s shell, %dp+%dn, seed %d (profiling case)" % (sp, int(npr), int(nne), int(sd))
+    if args.M != WORKLOAD["M"]:
+        schedule = [(m, n) for (m, n) in schedule if m < args.M] + [(args.M, schedule[-1][1])]
+    if args.sched_sweeps is not None:
+        schedule = [(m, min(n, args.sched_sweeps)) for (m, n) in schedule]
+    M = schedule[-1][0]
     prob = make_problem(w["space"], w["Np"], w["Nn"], w["two_Mz"], seed=w["seed"])
-    init = initial_mps(prob, M, w["mps_seed"])
-    d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
-    d.build_blocks(init)
+    init = initial_mps(prob, schedule[0][0], w["mps_seed"])
     N = prob.n_sites
-    start = N // 2 - 1 - args.warmup
-    setup, seq = _positions(N, max(start, 1), args.warmup + args.steps)
-    for (p, dr) in setup:
-        d.step(p, dr, M)
-    for (p, dr) in seq[:args.warmup]:
-        d.step(p, dr, M)
-    timed = seq[args.warmup:]
-    torch.cuda.synchronize()
-    c0 = d.counters()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed) + 1)]
-    stats = []
     with ClockSampler(local) as clk:
+        # ---- the whole job through the public API from host arrays (e2e): create the
+        # context (Hamiltonian copied from host memory), build the blocks from the host
+        # starting state, the sweep schedule, energies read back after every sweep
+        h2d = sum(int(a.nbytes) for a in (prob.species, prob.two_m, prob.eps, prob.v_idx,
+                                          prob.v_val, prob.order))
+        h2d += sum(int(np.asarray(a).nbytes) for a in init.flat())
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_job0 = time.perf_counter()
+        d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
+        d.build_blocks(init)
+        sweeps = []
+        n_job_steps = 0
+        for (Ms, ns) in schedule:
+            for _ in range(ns):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st, e = d.sweep(Ms)
+                e1.record()
+                e1.synchronize()
+                n_job_steps += len(st)
+                sweeps.append({"M": Ms, "s": e0.elapsed_time(e1) / 1e3, "energy": e,
+                               "products": sum(x["n_products"] for x in st),
+                               "heff_flops": sum(x["heff_flops"] * x["n_products"] for x in st),
+                               "heff_s": sum(x["heff_seconds"] for x in st),
+                               "max_step_ms": 1e3 * max(x["seconds"] for x in st)})
+        torch.cuda.synchronize()
+        t_job = time.perf_counter() - t_job0
+        job_flops = sum(x["heff_flops"] for x in sweeps)
+        # ---- timed two-site steps at the final M, centred on the middle of the chain
+        setup, warm, timed = _timed_window(N, args.steps, args.warmup)
+        for (p, dr) in setup + warm:
+            d.step(p, dr, M)
+        torch.cuda.synchronize()
+        c0 = d.counters()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed) + 1)]
+        stats = []
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -453,12 +498,12 @@ def run_gpu(args):
             torch.cuda.profiler.stop()
         if dist:
             dist.barrier()
-    c1 = d.counters()
+        c1 = d.counters()
+    clocks = clk.summary()
     free_b, total_b = torch.cuda.mem_get_info()
     dev_used_gb = (total_b - free_b) / 1e9
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(timed))]
-    total_s = sum(step_ms) / 1e3
-    total_s = max_over_ranks(total_s, dist)
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist)
     flops = sum(s["heff_flops"] * s["n_products"] for s in stats)
     heff_s = sum(s["heff_seconds"] for s in stats)
     heff_bytes = sum(s["heff_bytes"] * s["n_products"] for s in stats)
@@ -466,118 +511,127 @@ def run_gpu(args):
     value = replica_throughput(world, flops, total_s)
     peak, peak_kind = _peaks()
     achieved = heff_bytes / max(heff_s, 1e-12) / 1e9
-    p_e2e, _ = seq[-1]
-    # dot-orbital density matrix of the last timed step's wave function (wall clock of the
-    # whole call: piece lists on the host, two kernels, read-back)
-    dot = None
+    # ---- one FP64 sweep at M from the state the mixed path reached, step by step; at the
+    # middle of the chain (the heaviest superblocks) the mixed and the FP64 Davidson solve
+    # the identical superblock first (the energy gate), then the FP64 step continues from
+    # the FP64 eigenvector (its Davidson then needs one product: the sweep time is, if
+    # anything, slightly in FP64's favour)
+    fp64 = {}
     try:
-        ts = []
-        for _ in range(3):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, ent = d.dot_rdm(p_e2e)
-            ts.append(time.perf_counter() - t0)
-        size_last = d.psi_layout(p_e2e)["size"]
-        dot = {"position": p_e2e, "wall_ms": 1e3 * min(ts), "psi_elements": size_last,
-               "s_p": ent[0], "s_p1": ent[1], "I": ent[3]}
-    except Exception as exc:
-        dot = {"error": str(exc)}
-    lay = d.psi_layout(p_e2e)
-    # FP64 path on the same superblock: Davidson from the mixed eigenvector
-    psi_m = torch.empty(lay["size"], dtype=torch.float64, device="cuda")
-    e_mixed, st_m = d.davidson(p_e2e, out=psi_m, allow_noconv=True)
-    d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
-    c2 = d.counters()
-    e_fp64, st_d = d.davidson(p_e2e, guess=psi_m, allow_noconv=True)
-    c3 = d.counters()
-    fp64_tf = (c3["heff_flops"] - c2["heff_flops"]) / max(c3["heff_seconds"] - c2["heff_seconds"],
-                                                           1e-12) / 1e12
-    d.set_options(precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
+        finish = [(p, 0) for p in range(timed[-1][0] + 1, N - 2)] + \
+                 [(p, 1) for p in range(N - 3, 0, -1)]
+        for (p, dr) in finish:          # complete the mixed sweep the timed steps are in
+            d.step(p, dr, M)
+        seq = [(p, 0) for p in range(1, N - 2)] + [(p, 1) for p in range(N - 3, 0, -1)]
+        q = N // 2
+        fs = []
+        for _ in range(max(args.fp64_sweeps, 1) if args.fp64_sweeps > 0 else 0):
+            d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
+            ms, products, e = 0.0, 0, None
+            for (p, dr) in seq:
+                if p == q and dr == 0 and not fp64:
+                    d.set_options(precision=P.MIXED_FP32, dav_tol=1e-8,
+                                  dav_max_iter=args.max_iter)
+                    size = d.psi_layout(q)["size"]
+                    psi_m = torch.empty(size, dtype=torch.float64, device="cuda")
+                    e_mixed, st_m = d.davidson(q, out=psi_m, allow_noconv=True)
+                    d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
+                    c2 = d.counters()
+                    e_fp64, st_d = d.davidson(q, guess=psi_m, allow_noconv=True)
+                    c3 = d.counters()
+                    fp64 = {"position": q, "energy": e_fp64, "energy_mixed": e_mixed,
+                            "dE_mixed_vs_fp64": abs(e_mixed - e_fp64),
+                            "products_mixed": st_m["n_products"],
+                            "products_fp64_from_mixed_vector": st_d["n_products"],
+                            "converged": [st_m["converged"], st_d["converged"]],
+                            "heff_tflops": (c3["heff_flops"] - c2["heff_flops"])
+                            / max(c3["heff_seconds"] - c2["heff_seconds"], 1e-12) / 1e12}
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = d.step(p, dr, M)
+                e1.record()
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                products += st["n_products"]
+                e = st["energy"]
+            fs.append({"s": ms / 1e3, "energy": e, "products": products})
+        if fs:
+            fp64["sweep_s"] = statistics.median(x["s"] for x in fs)
+            fp64["sweeps"] = fs
+    except Exception as exc:        # a side measurement never takes the bench line down
+        fp64 = {"error": str(exc)}
     d.close()
     del d
-    # end to end through the public API: a fresh context from the host arrays of the
-    # Hamiltonian and the starting state (copied to the device inside the timed region),
-    # the block build, one full sweep at M, the energy read back to the host
-    e2e = None
-    sweep_s = None
-    if args.sweep:
-        h2d = sum(int(a.nbytes) for a in (prob.species, prob.two_m, prob.eps, prob.v_idx,
-                                          prob.v_val, prob.order))
-        h2d += sum(int(np.asarray(a).nbytes) for a in init.flat())
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dj = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8, dav_max_iter=args.max_iter)
-        dj.build_blocks(init)
-        t1 = time.perf_counter()
-        sw_steps, e_sweep = dj.sweep(M)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        sweep_s = t2 - t1
-        sw_flops = sum(s["heff_flops"] * s["n_products"] for s in sw_steps)
-        e2e = {"value": sw_flops / (t2 - t0) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 8 + len(sw_steps) * ctypes.sizeof(P.StepStats),
-               "job": "create from host arrays + block build + one sweep (%d steps, %d H_eff "
-                      "products) + energy read back; wall clock" % (len(sw_steps),
-                      sum(s["n_products"] for s in sw_steps)),
-               "build_s": t1 - t0, "sweep_energy": e_sweep}
-        dj.close()
-        del dj
-    clocks = clk.summary()
-    batch = None
-    if args.batch_mcap > 0:
-        batch = run_batch_compare(P, args.batch_mcap)
+    at_M = [x["s"] for x in sweeps if x["M"] == M]
+    sweep_s = statistics.median(at_M) if at_M else None
+    if rank == 0:
+        _emit("schedule", {"workload": wname, "sweeps": sweeps})
+        _emit("steps", {"positions": timed, "step_ms": step_ms,
+                        "energies": [s["energy"] for s in stats],
+                        "products": [s["n_products"] for s in stats],
+                        "heff_gflop": [s["heff_flops"] / 1e9 for s in stats],
+                        "phase_s": {k: c1[k] - c0[k] for k in ("t_enlarge", "t_super",
+                                                                "t_davidson", "t_truncate",
+                                                                "t_project", "t_predict",
+                                                                "t_sync")},
+                        "host_detail_s": [b - a for a, b in zip(c0["t_detail"], c1["t_detail"])],
+                        "superblock": {k: c1[k] for k in ("sb_blocks_l", "sb_blocks_r",
+                                                           "sb_terms", "sb_tiles",
+                                                           "sb_small_tiles", "sb_term_hist")}})
+        _emit("fp64", fp64)
+    batch = run_batch_compare(P, args.batch_mcap) if args.batch_mcap > 0 else None
+    if rank == 0 and batch:
+        _emit("batch", batch)
     precond = run_precond_compare(P) if args.precond else None
-    next_rows = None
+    if rank == 0 and precond:
+        _emit("precond", precond)
     if args.next_rows:
-        next_rows = run_next_rows(P, prob, init, M, e2e["sweep_energy"] if e2e else None)
+        nr = run_next_rows(P, prob, init, M, None)
+        if rank == 0:
+            _emit("next_rows", nr)
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = _cpu_baseline_subprocess(args.steps, args.warmup)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / len(timed),
+        "steps": len(timed), "warmup": len(warm), "ms_per_step": 1e3 * total_s / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": wname, "M": M, "positions": timed,
-                   "precision": "FP32 contractions, FP64 Davidson/eigensolver/energy",
+        "config": {"workload": wname, "M": M,
+                   "positions": "%d..%d left to right" % (timed[0][0], timed[-1][0]),
+                   "schedule": "+".join("%d(%d)" % x for x in schedule),
+                   "precision": "FP32 contractions (split-TF32 tensor cores), FP64 "
+                                "Davidson/SVD/energy",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: %.0f MB of operator blocks per H_eff product"
                          % (heff_bytes / max(nprod, 1) / 1e6)},
         "heff": {"tflops_device": flops / max(heff_s, 1e-12) / 1e12, "products": nprod,
-                 "device_s": heff_s, "flops_per_product": flops / max(nprod, 1),
-                 "bytes_per_product": heff_bytes / max(nprod, 1)},
-        "sweep_s": sweep_s,
-        "fp64": {"heff_tflops": fp64_tf, "energy": e_fp64, "products": st_d["n_products"],
-                 "energy_mixed": e_mixed, "dE_mixed_vs_fp64": abs(e_mixed - e_fp64)},
+                 "gflop_per_product": flops / max(nprod, 1) / 1e9,
+                 "share_of_steps": heff_s / max(total_s, 1e-12)},
+        "sweep_s": {"mixed_median_at_M": sweep_s, "fp64_at_M": fp64.get("sweep_s"),
+                    "mixed_energy": sweeps[-1]["energy"] if sweeps else None,
+                    "fp64_energy": fp64["sweeps"][-1]["energy"] if fp64.get("sweeps") else None},
+        "fp64": {k: fp64.get(k) for k in ("heff_tflops", "dE_mixed_vs_fp64", "position")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": HEFF_TRAFFIC_BYTES if not args.workload and M == WORKLOAD["M"]
-                     else None,
-                     "kernel": "H_eff product: k_pad_psi + k_heff_small + k_heff_tc + k_heff_reduce + k_to_f64, CUDA events on the context stream around each product",
-                     "peak_kind": peak_kind},
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "mixed H_eff product (its kernels between CUDA events on the "
+                               "context stream)", "peak_kind": peak_kind},
         "cpu_baseline": cpu,
-        "batch": batch,
-        "precond": precond,
-        "next_rows": next_rows,
-        "dot_rdm": dot,
-        "e2e": e2e,
+        "e2e": {"value": job_flops / t_job / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": h2d / max(n_job_steps, 1),
+                "d2h_bytes_per_step": ctypes.sizeof(P.StepStats) + 8,
+                "job": "create from host arrays + block build + the schedule (%d sweeps, %d "
+                       "steps) with every sweep's step records and energy read back; wall "
+                       "clock %.1f s; h2d %d bytes per job" % (len(sweeps), n_job_steps,
+                                                               t_job, h2d)},
         "gpu_launches": int(c1["launches"] - c0["launches"]),
-        "device_mem_used_gb": dev_used_gb,
-        "phase_s": {k: c1[k] - c0[k] for k in ("t_enlarge", "t_super", "t_davidson",
-                                               "t_truncate", "t_project", "t_predict",
-                                               "t_sync", "t_enlarge_host", "t_upload")},
-        "upload_bytes": c1["upload_bytes"] - c0["upload_bytes"],
-        "pool_mallocs": c1["pool_mallocs"] - c0["pool_mallocs"],
-        "host_detail_s": [b - a for a, b in zip(c0["t_detail"], c1["t_detail"])],
-        "superblock": {k: c1[k] for k in ("sb_blocks_l", "sb_blocks_r", "sb_terms", "sb_tiles",
-                                           "sb_small_tiles", "sb_term_hist",
-                                           "sb_kernel_flops")},
+        "device_mem_used_gb": round(dev_used_gb, 2),
         "clocks": clocks,
-        "energies": [s["energy"] for s in stats],
-        "step_ms": step_ms,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -593,9 +647,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--M", type=int, default=WORKLOAD["M"])
     ap.add_argument("--max-iter", type=int, default=100)
-    ap.add_argument("--sweep", type=int, default=1)
+    ap.add_argument("--sched-sweeps", type=int, default=None,
+                    help="cap the sweeps per M of the schedule (profiling)")
+    ap.add_argument("--fp64-sweeps", type=int, default=1,
+                    help="FP64 sweeps at the final M after the mixed schedule (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-mcap", type=int, default=256,
+    ap.add_argument("--batch-mcap", type=int, default=2048,
                     help="M cap of the 32-instance batch-vs-loop comparison (0: skip)")
     ap.add_argument("--precond", type=int, default=1,
                     help="learned vs diagonal preconditioner comparison (0: skip)")

@@ -361,6 +361,35 @@ int dmrg_mlp_loss_grad(dmrg_ctx* ctx, int32_t precision, const double* params, c
                        const double* T, int64_t B, double* loss, double* grad);
 int64_t dmrg_mlp_n_params(void);
 
+/* Work split of the kernels (not in the paper; results agree to rounding whatever the
+ * split, which the tests check).
+ *   heff_big_edge: an output block of H_eff psi whose own dimensions or whose terms' input
+ *     dimensions exceed this edge is computed by two grouped GEMM passes (T_k = psi R_k^T
+ *     into a device scratch, then psi' = sum_k s_k L_k T_k; split-TF32 tensor cores in
+ *     DMRG_MIXED_FP32, FP64 tiles in DMRG_FP64); smaller blocks by the fused tile kernels.
+ *     0 = the fused kernels for every block; default 128 (measured on the headline
+ *     workload at M = 4096: the grouped passes are as fast as the fused kernels on blocks
+ *     of a few hundred states and 20x more accurate; on narrower blocks the fused kernels
+ *     are faster).
+ *   svd_cluster: thread-block cluster size of the truncation's SVDs: 0 = chosen per sector
+ *     (default), or 1, 8 or 16 for every sector whose shared-memory share fits.
+ * Call between steps: the superblock held by the context is dropped and rebuilt at its next
+ * use (a wave function held for truncation must be recomputed).  DMRG_EINVAL for values
+ * out of range (heff_big_edge < 0 or > 4096, svd_cluster not 0, 1, 8 or 16). */
+typedef struct {
+  int32_t heff_big_edge;
+  int32_t svd_cluster;
+} dmrg_tuning;
+int dmrg_set_tuning(dmrg_ctx* ctx, const dmrg_tuning* t);
+int dmrg_get_tuning(dmrg_ctx* ctx, dmrg_tuning* t);
+
+/* Number of operator products L_k (x) R_k across bond b (0 <= b <= N-2) of the normal /
+ * complementary operator partition built at dmrg_create: the terms the superblock
+ * Hamiltonian sums over when the cut lies at bond b (labels that cannot connect the vacuum
+ * to the full Hamiltonian are pruned).  Host data only, no device work.  DMRG_EINVAL for b
+ * out of range. */
+int dmrg_partition_terms(dmrg_ctx* ctx, int32_t b, int32_t* n_terms);
+
 /* Read the cumulative counters. */
 int dmrg_get_counters(dmrg_ctx* ctx, dmrg_counters* out);
 

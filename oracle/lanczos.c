@@ -56,12 +56,8 @@ typedef struct {
 } Species;
 
 static uint64_t mix64(uint64_t x) {
-  x ^= x >> 33;
-  x *= 0xff51afd7ed558ccdULL;
-  x ^= x >> 33;
-  x *= 0xc4ceb9fe1a85ec53ULL;
-  x ^= x >> 33;
-  return x;
+  x *= 0x9E3779B97F4A7C15ULL;   /* Fibonacci hashing: the table size is a power of two */
+  return x ^ (x >> 29);
 }
 
 static int species_lookup(const Species* sp, uint64_t key) {
@@ -182,6 +178,8 @@ typedef struct {
   int* b_gn;
   int64_t* b_base;    /* [n_blocks + 1] */
   int* gp_block;      /* proton group -> block (or -1) */
+  int64_t* p_base;    /* proton configuration -> b_base + rank * (block's neutron count), or -1 */
+  int* n_group;       /* neutron configuration -> its group (== the block's gn when valid) */
   int64_t dim;
   /* two-body list in CSR by annihilated pair (k, l), k < l: pair index k * N + l */
   int64_t* pair_ptr;  /* [N*N + 1] */
@@ -197,6 +195,7 @@ static void sector_free(Sector* S) {
   free(S->b_gn);
   free(S->b_base);
   free(S->gp_block);
+  free(S->p_base);
   free(S->pair_ptr);
   free(S->ti);
   free(S->tj);
@@ -248,6 +247,17 @@ static int sector_build(Sector* S, int N, const int8_t* species, const int8_t* t
   }
   S->b_base[S->n_blocks] = base;
   S->dim = base;
+  S->p_base = (int64_t*)malloc(sizeof(int64_t) * (size_t)S->P.n_conf);
+  for (int ip = 0; ip < S->P.n_conf; ++ip) {
+    const int b = S->gp_block[S->P.group[ip]];
+    if (b < 0) {
+      S->p_base[ip] = -1;
+      continue;
+    }
+    const int gn = S->b_gn[b];
+    S->p_base[ip] = S->b_base[b] + (int64_t)S->P.rank[ip] * (S->Nn.g_start[gn + 1] - S->Nn.g_start[gn]);
+  }
+  S->n_group = S->Nn.group;
   /* two-body terms grouped by the annihilated pair */
   const int64_t npair = (int64_t)N * N;
   S->pair_ptr = (int64_t*)calloc((size_t)(npair + 1), sizeof(int64_t));
@@ -280,12 +290,10 @@ static int64_t sector_index(const Sector* S, uint64_t s) {
   const int ip = species_lookup(&S->P, s & S->pmask_all);
   const int in = species_lookup(&S->Nn, s & S->nmask_all);
   if (ip < 0 || in < 0) return -1;
-  const int b = S->gp_block[S->P.group[ip]];
-  if (b < 0) return -1;
-  const int gn = S->b_gn[b];
-  if (S->Nn.two_m[in] != S->Nn.g_two_m[gn]) return -1;
-  const int dn = S->Nn.g_start[gn + 1] - S->Nn.g_start[gn];
-  return S->b_base[b] + (int64_t)S->P.rank[ip] * dn + S->Nn.rank[in];
+  const int64_t pb = S->p_base[ip];
+  if (pb < 0) return -1;
+  if (S->n_group[in] != S->b_gn[S->gp_block[S->P.group[ip]]]) return -1;
+  return pb + S->Nn.rank[in];
 }
 
 /* determinant mask of basis index r */
@@ -322,18 +330,14 @@ static void apply_rows(const Sector* S, const double* x, double* y, int64_t r0, 
       for (int b = a + 1; b < n; ++b) {
         const int k = occ[a], l = occ[b];
         const int64_t p0 = S->pair_ptr[(int64_t)k * N + l], p1 = S->pair_ptr[(int64_t)k * N + l + 1];
+        /* c+_i c+_j c_l c_k |s>: c_k then c_l act first, the same for every (i, j) */
+        const int sgkl = parity_below(s, k) ^ parity_below(s ^ (1ULL << k), l);
+        const uint64_t base = s ^ (1ULL << k) ^ (1ULL << l);
         for (int64_t t = p0; t < p1; ++t) {
           const int i = S->ti[t], j = S->tj[t];
-          /* c+_i c+_j c_l c_k |s> */
-          int sg = parity_below(s, k);
-          uint64_t u = s ^ (1ULL << k);
-          sg ^= parity_below(u, l);
-          u ^= 1ULL << l;
-          if ((u >> j) & 1ULL) continue;
-          sg ^= parity_below(u, j);
-          u |= 1ULL << j;
-          if ((u >> i) & 1ULL) continue;
-          sg ^= parity_below(u, i);
+          if (base & ((1ULL << i) | (1ULL << j))) continue;   /* i or j already occupied */
+          uint64_t u = base | (1ULL << j);
+          const int sg = sgkl ^ parity_below(base, j) ^ parity_below(u, i);
           u |= 1ULL << i;
           const int64_t c = sector_index(S, u);
           if (c < 0) continue;   /* cannot happen for terms that conserve N_p, N_n, 2M */

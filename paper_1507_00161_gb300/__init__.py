@@ -25,7 +25,7 @@ MIXED_FP32 = 1
 EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks",
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
-            "dmrg_rdm_eigh",
+            "dmrg_rdm_eigh", "dmrg_set_tuning", "dmrg_get_tuning", "dmrg_partition_terms",
             "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_dot_rdm",
             "dmrg_get_counters",
             "dmrg_heff_cost",
@@ -82,6 +82,10 @@ class StepStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("heff_big_edge", ctypes.c_int32), ("svd_cluster", ctypes.c_int32)]
+
+
 class BatchStats(ctypes.Structure):
     _fields_ = [("products", ctypes.c_int64), ("heff_seconds", ctypes.c_double),
                 ("launches", ctypes.c_int64)]
@@ -135,6 +139,9 @@ def load_library(path: str = LIB_PATH):
         "dmrg_set_roots": [P, i32],
         "dmrg_dot_rdm": [P, i32, P, P],
         "dmrg_rdm_eigh": [P, i32, i32, i32, P, P, P, P, P, P],
+        "dmrg_set_tuning": [P, ctypes.POINTER(Tuning)],
+        "dmrg_partition_terms": [P, i32, P],
+        "dmrg_get_tuning": [P, ctypes.POINTER(Tuning)],
         "dmrg_mlp_reset": [P, ctypes.c_uint64],
         "dmrg_mlp_harvest": [P, i32, i32],
         "dmrg_mlp_train": [P, i32, i32, dbl, ctypes.c_uint64, P, P],
@@ -272,6 +279,24 @@ class DMRG:
         ent = np.zeros(4)
         self._check(self.lib.dmrg_dot_rdm(self.h, int(p), _np_ptr(rho), _np_ptr(ent)))
         return rho.reshape(4, 4), tuple(float(x) for x in ent)
+
+    def partition_terms(self, b):
+        """Number of operator products across bond b of the operator partition."""
+        n = ctypes.c_int32()
+        self._check(self.lib.dmrg_partition_terms(self.h, int(b), ctypes.byref(n)))
+        return n.value
+
+    def tuning(self):
+        t = Tuning()
+        self._check(self.lib.dmrg_get_tuning(self.h, ctypes.byref(t)))
+        return {"heff_big_edge": t.heff_big_edge, "svd_cluster": t.svd_cluster}
+
+    def set_tuning(self, heff_big_edge=None, svd_cluster=None):
+        """Work split of the kernels (dmrg_set_tuning); None keeps the current value."""
+        cur = self.tuning()
+        t = Tuning(int(cur["heff_big_edge"] if heff_big_edge is None else heff_big_edge),
+                   int(cur["svd_cluster"] if svd_cluster is None else svd_cluster))
+        self._check(self.lib.dmrg_set_tuning(self.h, ctypes.byref(t)))
 
     def rdm_eigh(self, p, direction, cluster=0, vectors=True):
         """Per-sector spectrum (and eigenvectors) of the reduced density matrix of the wave

@@ -292,7 +292,10 @@ struct DevTaskList {
   double flops = 0;      // algorithmic flops of the list
   // base_elems[b]: elements addressable through base b (0 = unused); every operand range
   // is checked against it on the host before the list reaches the device
-  void build(const TaskList& L, const int64_t* base_elems, cudaStream_t s);
+  // small_limit: tasks of at most this many outputs run one warp each; the others are cut
+  // into 64 x 64 tiles (0: every task tiled, the form the tensor-core engine wants)
+  void build(const TaskList& L, const int64_t* base_elems, cudaStream_t s,
+             int64_t small_limit = 1024);
 };
 
 
@@ -315,8 +318,16 @@ void validate_copy_tasks(const CopyList& L, const int64_t* base_elems);
 // ---------------------------------------------------------------------------------------
 // kernels (kernels.cu)
 // ---------------------------------------------------------------------------------------
+// active (optional, device): the launch does nothing while active[0] == 0 (batch mode)
 template <class T>
-void run_gemm_tasks(const DevTaskList& L, const Bases<T>& b, int beta_zero, cudaStream_t s);
+void run_gemm_tasks(const DevTaskList& L, const Bases<T>& b, int beta_zero, cudaStream_t s,
+                    const int32_t* active = nullptr);
+// the same task lists on the tensor cores (tgemm.cu): operands of types TA, TB (float or
+// double) split into TF32 high + low parts, three MMAs per product, FP32 accumulation, C of
+// type TC; tasks of at most 1024 outputs with FP32 FMAs on the CUDA cores
+template <class TA, class TB, class TC>
+void run_gemm_tasks_tc(const DevTaskList& L, const Bases<void>& b, int beta_zero, cudaStream_t s,
+                       const int32_t* active = nullptr);
 template <class T>
 void run_copy_tasks(const CopyTask* d_tasks, int64_t n_tasks, const CopyTerm* d_terms,
                     const Bases<T>& b, cudaStream_t s);
@@ -438,6 +449,9 @@ struct HeffPtrs {
 // output blocks with m, n <= kSmallEdge whose terms all have dLi, dRi <= kSmallEdge go
 // to the warp-per-tile CUDA-core product (heff_small.cu); its tiles are whole blocks
 constexpr int kSmallEdge = 16;
+// output blocks with a dimension of their own or of one of their terms above kBigEdge go to
+// the grouped GEMM passes (tgemm.cu / kernels.cu) instead of the fused tile kernels
+constexpr int kBigEdge = 128;
 template <class T>
 void heff_small(const HeffTile* d_tiles, int64_t n_tiles, const HeffItem* d_items,
                 const HeffPtrs<T>& ptrs, cudaStream_t s);

@@ -155,6 +155,12 @@ struct Super {
   int64_t size = 0;
   DevTaskList st1, st2;
   bool two_stage_ready = false;
+  // output blocks too wide for the fused tile kernels (a dimension of the block or of one
+  // of its terms above 32): two grouped GEMM passes, T_k = psi(b_in) R_k^T into a scratch,
+  // then psi'(b_out) = sum_k s_k L_k T_k (every such output block written by one task)
+  DevTaskList big1, big2;
+  int64_t big_t_elems = 0;
+  int64_t n_big_blocks = 0;
   struct Term {
     int64_t lb, rb;
     int bin, bout;
@@ -225,6 +231,8 @@ struct dmrg_ctx {
   // scratch
   dmrg::DevBuf<double> T, tmp, rho, eV, eVs, ew, sel;
   dmrg::DevBuf<int> noconv;    // set by a truncation SVD that reached its sweep limit
+  int big_edge = dmrg::kBigEdge;   // output blocks wider than this: grouped GEMM passes (0: never)
+  int svd_cluster = 0;         // forced cluster size of the truncation SVDs (0: per sector)
   int64_t eig_noconv = 0;      // truncations with such an SVD
   dmrg::DevBuf<float> f32a, f32b, f32T, part32;
   dmrg::DevBuf<double> part64, xpad64, ybat64;
@@ -877,6 +885,9 @@ static void project(Ctx& c, OpSet& E, const Iso& iso, OpSet& out) {
   tp = wall();
   project_small(dts.p, int64_t(small.size()), dD.p, dm.p, duo.p, E.data.p, iso.data.p,
                 out.data.p, c.stream);
+  // FP64 in both precisions: the stored operators must keep the Hermitian pairing of the
+  // normal and complementary operators to FP64 rounding; split-TF32 products left the pairs
+  // unequal at ~1e-6 relative, which floored the Davidson residual of the next steps
   project_blocks(dt.p, dtb1.p, tb1.back(), dtb2.p, tb2.back(), int64_t(tasks.size()), dD.p,
                  dm.p, duo.p, E.data.p, iso.data.p, c.tmp.p, out.data.p, c.stream);
   sync(c);
@@ -1036,22 +1047,26 @@ static void build_super(Ctx& c, int p) {
   const int G = 64, Gs = 16;
   std::vector<int64_t> i_beg(nb + 1, 0), t_beg(nb + 1, 0), s_beg(nb + 1, 0), r_beg(nb + 1, 0),
       p_beg(nb + 1, 0);
-  std::vector<char> small_bo(nb, 0);
+  std::vector<char> small_bo(nb, 0), big_bo(nb, 0);
   for (int bo = 0; bo < nb; ++bo) {
     const int ni = int(by_out[bo].size());
     bool sm = sb->bdl[bo] <= kSmallEdge && sb->bdr[bo] <= kSmallEdge;
-    for (int j = 0; j < ni && sm; ++j) {
+    int wide = std::max(sb->bdl[bo], sb->bdr[bo]);
+    for (int j = 0; j < ni; ++j) {
       const int bin = by_out[bo][j].bin;
-      sm = sb->bdl[bin] <= kSmallEdge && sb->bdr[bin] <= kSmallEdge;
+      sm = sm && sb->bdl[bin] <= kSmallEdge && sb->bdr[bin] <= kSmallEdge;
+      wide = std::max(wide, std::max(sb->bdl[bin], sb->bdr[bin]));
     }
     small_bo[bo] = sm;
+    const bool big = !sm && c.big_edge > 0 && wide > c.big_edge;
+    big_bo[bo] = big;
     const int groups = sm ? std::max(1, (ni + Gs - 1) / Gs) : std::max(1, (ni + G - 1) / G);
     const int64_t tiles = sm ? 1 : int64_t((sb->bdl[bo] + 31) / 32) * ((sb->bdr[bo] + 31) / 32);
     i_beg[bo + 1] = i_beg[bo] + ni;
-    t_beg[bo + 1] = t_beg[bo] + (sm ? 0 : tiles * groups);
+    t_beg[bo + 1] = t_beg[bo] + (sm || big ? 0 : tiles * groups);
     s_beg[bo + 1] = s_beg[bo] + (sm ? groups : 0);
-    r_beg[bo + 1] = r_beg[bo] + (groups > 1 ? tiles : 0);
-    p_beg[bo + 1] = p_beg[bo] + (groups > 1 ? int64_t(groups) * sb->bdl[bo] * sb->bdr[bo] : 0);
+    r_beg[bo + 1] = r_beg[bo] + (groups > 1 && !big ? tiles : 0);
+    p_beg[bo + 1] = p_beg[bo] + (groups > 1 && !big ? int64_t(groups) * sb->bdl[bo] * sb->bdr[bo] : 0);
   }
   DMRG_REQUIRE(i_beg[nb] < (int64_t(1) << 31), DMRG_EINVAL, "superblock has too many terms");
   struct TileCost {
@@ -1102,6 +1117,7 @@ static void build_super(Ctx& c, int p) {
       bo_bytes[bo] = by;
       bo_hist[bo] = hist;
       bo_toff[bo] = to;
+      if (big_bo[bo]) continue;   // the grouped GEMM passes below
       const bool sm = small_bo[bo];
       const int GG = sm ? Gs : G, edge = sm ? kSmallEdge : 32;
       const int groups = std::max(1, (i1 - i0 + GG - 1) / GG);
@@ -1215,6 +1231,41 @@ static void build_super(Ctx& c, int p) {
     sb->n_fred = int64_t(sb->h_red.size());
     sb->p_elems = pelems;
   }
+  {
+    // grouped GEMM passes of the big output blocks
+    TaskList g1, g2;
+    int64_t toff2 = 0;
+    for (int bo = 0; bo < nb; ++bo) {
+      if (!big_bo[bo]) continue;
+      ++sb->n_big_blocks;
+      const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
+      g2.begin_task(Operand{sb->boff[bo], B_Y, dRo}, dLo, dRo);
+      for (int64_t j = i_beg[bo]; j < i_beg[bo + 1]; ++j) {
+        const Super::Term& tm = sb->terms_host[j];
+        const int dLi = sb->bdl[tm.bin], dRi = sb->bdr[tm.bin];
+        g1.begin_task(Operand{toff2, B_T, dRo}, dLi, dRo);
+        g1.add_term(Operand{sb->pad_off[tm.bin], B_X, dRi},
+                    Operand{sb->R.blocks[tm.rb].off, B_ROPS, dRi}, dRi, 2, 1.0);
+        g2.add_term(Operand{sb->L.blocks[tm.lb].off, B_LOPS, dLi}, Operand{toff2, B_T, dRo}, dLi,
+                    0, tm.sign);
+        toff2 += int64_t(dLi) * dRo;
+      }
+    }
+    sb->big_t_elems = toff2;
+    if (sb->n_big_blocks) {
+      int64_t be[NBASE] = {0};
+      be[B_X] = sb->pad_size;
+      be[B_Y] = sb->size;
+      be[B_T] = std::max<int64_t>(toff2, 1);
+      be[B_LOPS] = sb->L.n_elems;
+      be[B_ROPS] = sb->R.n_elems;
+      // the tensor-core engine takes every task as tiles; the FP64 one runs small tasks
+      // one warp each
+      const int64_t lim = c.opt.precision == DMRG_FP64 ? 1024 : 0;
+      sb->big1.build(g1, be, c.stream, lim);
+      sb->big2.build(g2, be, c.stream, lim);
+    }
+  }
   lap(2);
   // diagonal tasks: terms that keep the sector (Delta q = 0)
   std::vector<DiagTask> dt;
@@ -1293,8 +1344,9 @@ static void ensure_two_stage(Ctx& c, Super& sb) {
 }
 
 static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st) {
-  // every psi' element is written by exactly one fused tile (blocks without terms get
-  // zero-term tiles), so no clearing pass is needed
+  // every psi' element is written by exactly one fused tile or one grouped-GEMM task of the
+  // big output blocks (blocks without terms get zero-term tiles or tasks), so no clearing
+  // pass is needed
   const int nb = int(sb.bL.size());
   if (c.opt.precision == DMRG_FP64) {
     c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
@@ -1309,6 +1361,17 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st)
     heff_small<double>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
     heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr,
                        st);
+    if (sb.n_big_blocks) {
+      c.T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      Bases<double> bb{};
+      bb.p[B_LOPS] = sb.L.data.p;
+      bb.p[B_ROPS] = sb.R.data.p;
+      bb.p[B_X] = c.xpad64.p;
+      bb.p[B_Y] = y;
+      bb.p[B_T] = c.T.p;
+      run_gemm_tasks<double>(sb.big1, bb, 1, st);
+      run_gemm_tasks<double>(sb.big2, bb, 1, st);
+    }
   } else {
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
     c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
@@ -1322,6 +1385,17 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st)
     ptr.P[0] = c.part32.p;
     heff_small<float>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
     heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, st);
+    if (sb.n_big_blocks) {
+      c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      Bases<void> bb{};
+      bb.p[B_LOPS] = sb.L.data32.p;
+      bb.p[B_ROPS] = sb.R.data32.p;
+      bb.p[B_X] = c.xpad32.p;
+      bb.p[B_Y] = c.f32b.p;
+      bb.p[B_T] = c.f32T.p;
+      run_gemm_tasks_tc<float, float, float>(sb.big1, bb, 1, st);
+      run_gemm_tasks_tc<float, float, float>(sb.big2, bb, 1, st);
+    }
     to_f64(c.f32b.p, y, sb.size, st);
   }
 }
@@ -1934,7 +2008,7 @@ static TruncResult truncate_renormalize(Ctx& c, int p, int dir, int M) {
     tr.trunc = 0.0;
     tr.kept = int(total);
   } else {
-    const bool noconv = rdm_eigh(c, sb, dir, RL, 0);
+    const bool noconv = rdm_eigh(c, sb, dir, RL, c.svd_cluster);
     if (noconv) {
       tr.noconv = true;
       c.eig_noconv += 1;
@@ -2685,6 +2759,20 @@ extern "C" int dmrg_block_sectors(dmrg_ctx* c, int32_t side, int32_t b, int32_t*
   });
 }
 
+// drop the superblock held by the context (rebuilt at its next use), after any Rayleigh
+// quotient still reading it
+static void drop_superblock(Ctx& c) {
+  if (!c.sb) return;
+  settle_energy(c);
+  if (c.rq_pending) {
+    launch_rq(c);
+    DMRG_CUDA(cudaEventSynchronize(c.rq_out));
+  }
+  DMRG_CUDA(cudaStreamSynchronize(c.stream));
+  if (c.rq_sb == c.sb.get()) c.rq_sb = nullptr;
+  c.sb.reset();
+}
+
 extern "C" int dmrg_set_options(dmrg_ctx* c, const dmrg_options* opt) {
   return guarded(c, [&] {
     DMRG_REQUIRE(opt != nullptr, DMRG_EINVAL, "options are NULL");
@@ -2697,14 +2785,40 @@ extern "C" int dmrg_set_options(dmrg_ctx* c, const dmrg_options* opt) {
                                      opt->reserved0 == DMRG_PRECOND_DIAG),
                  DMRG_EINVAL, "two-state targeting needs DMRG_FP64 and the diagonal preconditioner");
     const bool prec_changed = opt->precision != c->opt.precision;
+    // byte counts, FP32 operator shadows and product lists depend on the precision
+    if (prec_changed) drop_superblock(*c);
     c->opt = *opt;
     c->stream = static_cast<cudaStream_t>(opt->stream);
-    if (prec_changed && c->sb) {
-      // byte counts and FP32 operator shadows depend on the precision
-      int p = c->sb->p;
-      c->sb.reset();
-      (void)p;
-    }
+  });
+}
+
+extern "C" int dmrg_set_tuning(dmrg_ctx* c, const dmrg_tuning* t) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(t != nullptr, DMRG_EINVAL, "NULL tuning");
+    DMRG_REQUIRE(t->heff_big_edge >= 0 && t->heff_big_edge <= 4096, DMRG_EINVAL,
+                 "heff_big_edge must lie in [0, 4096]");
+    DMRG_REQUIRE(t->svd_cluster == 0 || t->svd_cluster == 1 || t->svd_cluster == 8 ||
+                     t->svd_cluster == 16,
+                 DMRG_EINVAL, "svd_cluster must be 0, 1, 8 or 16");
+    c->big_edge = t->heff_big_edge;
+    c->svd_cluster = t->svd_cluster;
+    drop_superblock(*c);   // its product lists follow the old split: rebuilt at the next use
+  });
+}
+
+extern "C" int dmrg_get_tuning(dmrg_ctx* c, dmrg_tuning* t) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(t != nullptr, DMRG_EINVAL, "NULL tuning");
+    t->heff_big_edge = c->big_edge;
+    t->svd_cluster = c->svd_cluster;
+  });
+}
+
+extern "C" int dmrg_partition_terms(dmrg_ctx* c, int32_t b, int32_t* n_terms) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(n_terms != nullptr, DMRG_EINVAL, "NULL output");
+    DMRG_REQUIRE(b >= 0 && b <= c->N - 2, DMRG_EINVAL, "bond out of range [0, N-2]");
+    *n_terms = int32_t(c->mpo.labels[b + 1].size());
   });
 }
 
@@ -3002,6 +3116,19 @@ static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
     }
     heff_small<double>(B.stiles.p, B.n_stiles, B.items.p, ptr, B.bs);
     heff_fused<double>(B.tiles.p, B.n_tiles, B.items.p, B.red.p, B.n_red, ptr, B.bs);
+    for (int i : inst) {   // big output blocks: grouped GEMM passes per instance
+      Ctx& c = *B.ctx[i];
+      Super& sb = *c.sb;
+      if (!sb.n_big_blocks) continue;
+      Bases<double> bb{};
+      bb.p[B_LOPS] = sb.L.data.p;
+      bb.p[B_ROPS] = sb.R.data.p;
+      bb.p[B_X] = c.xpad64.p;
+      bb.p[B_Y] = c.ybat64.p;
+      bb.p[B_T] = c.T.p;
+      run_gemm_tasks<double>(sb.big1, bb, 1, B.bs, act + i);
+      run_gemm_tasks<double>(sb.big2, bb, 1, B.bs, act + i);
+    }
     for (int i : inst) {
       Ctx& c = *B.ctx[i];
       out_to_f64_ind<double>(c.ybat64.p, &B.d_tab->out[i], c.sb->size, act + i, B.bs);
@@ -3022,6 +3149,19 @@ static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
     }
     heff_small<float>(B.stiles.p, B.n_stiles, B.items.p, ptr, B.bs);
     heff_tc(B.tiles.p, B.n_tiles, B.items.p, B.red.p, B.n_red, ptr, B.bs);
+    for (int i : inst) {   // big output blocks: grouped GEMM passes per instance
+      Ctx& c = *B.ctx[i];
+      Super& sb = *c.sb;
+      if (!sb.n_big_blocks) continue;
+      Bases<void> bb{};
+      bb.p[B_LOPS] = sb.L.data32.p;
+      bb.p[B_ROPS] = sb.R.data32.p;
+      bb.p[B_X] = c.xpad32.p;
+      bb.p[B_Y] = c.f32b.p;
+      bb.p[B_T] = c.f32T.p;
+      run_gemm_tasks_tc<float, float, float>(sb.big1, bb, 1, B.bs, act + i);
+      run_gemm_tasks_tc<float, float, float>(sb.big2, bb, 1, B.bs, act + i);
+    }
     for (int i : inst) {
       Ctx& c = *B.ctx[i];
       out_to_f64_ind<float>(c.f32b.p, &B.d_tab->out[i], c.sb->size, act + i, B.bs);
@@ -3039,10 +3179,12 @@ static void batch_buffers(dmrg_batch& B, const std::vector<int>& inst) {
       c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
       c.xpad64.alloc(sb.pad_size);
       c.ybat64.alloc(std::max<int64_t>(sb.size, 1));
+      if (sb.n_big_blocks) c.T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
     } else {
       c.f32b.alloc(std::max<int64_t>(sb.size, 1));
       c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
       c.xpad32.alloc(sb.pad_size);
+      if (sb.n_big_blocks) c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
     }
   }
 }

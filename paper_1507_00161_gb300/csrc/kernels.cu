@@ -38,7 +38,9 @@ template <class T>
 __global__ void __launch_bounds__(256) k_gemm_small(const GemmTask* __restrict__ tasks,
                                                     int64_t n_tasks,
                                                     const GemmTerm* __restrict__ terms,
-                                                    Bases<T> b, int beta_zero) {
+                                                    Bases<T> b, int beta_zero,
+                                                    const int32_t* __restrict__ active) {
+  if (active && !active[0]) return;
   int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kWarp;
   int lane = threadIdx.x & (kWarp - 1);
   if (w >= n_tasks) return;
@@ -72,7 +74,9 @@ template <class T>
 __global__ void __launch_bounds__(256) k_gemm_tiled(const GemmTile* __restrict__ tiles,
                                                     const GemmTask* __restrict__ tasks,
                                                     const GemmTerm* __restrict__ terms,
-                                                    Bases<T> b, int beta_zero) {
+                                                    Bases<T> b, int beta_zero,
+                                                    const int32_t* __restrict__ active) {
+  if (active && !active[0]) return;
   __shared__ T As[TK][TM + 1];
   __shared__ T Bs[TK][TN + 1];
   const GemmTile tl = tiles[blockIdx.x];
@@ -131,7 +135,6 @@ __global__ void __launch_bounds__(256) k_gemm_tiled(const GemmTile* __restrict__
   }
 }
 
-static const int kSmallLimit = 1024;   // M*N of a task run by one warp
 
 static void check_range(const Operand& o, int rows, int cols, const int64_t* be,
                         const char* what) {
@@ -152,7 +155,8 @@ void validate_copy_tasks(const CopyList& L, const int64_t* be) {
   }
 }
 
-void DevTaskList::build(const TaskList& L, const int64_t* be, cudaStream_t s) {
+void DevTaskList::build(const TaskList& L, const int64_t* be, cudaStream_t s,
+                        int64_t small_limit) {
   for (const auto& t : L.tasks) {
     check_range(t.C, t.M, t.N, be, "C");
     for (int j = t.t0; j < t.t1; ++j) {
@@ -170,7 +174,7 @@ void DevTaskList::build(const TaskList& L, const int64_t* be, cudaStream_t s) {
   for (const auto& t : L.tasks) {
     for (int j = t.t0; j < t.t1; ++j) flops += 2.0 * t.M * t.N * double(L.terms[j].K);
     if (t.M <= 0 || t.N <= 0) continue;
-    if (int64_t(t.M) * t.N <= kSmallLimit) {
+    if (int64_t(t.M) * t.N <= small_limit) {
       sm.push_back(t);
     } else {
       int id = int(lg.size());
@@ -189,21 +193,25 @@ void DevTaskList::build(const TaskList& L, const int64_t* be, cudaStream_t s) {
 }
 
 template <class T>
-void run_gemm_tasks(const DevTaskList& L, const Bases<T>& b, int beta_zero, cudaStream_t s) {
+void run_gemm_tasks(const DevTaskList& L, const Bases<T>& b, int beta_zero, cudaStream_t s,
+                    const int32_t* active) {
   if (L.n_small) {
     int64_t threads = L.n_small * kWarp;
     int blocks = int((threads + 255) / 256);
-    k_gemm_small<T><<<blocks, 256, 0, s>>>(L.small_tasks.p, L.n_small, L.terms.p, b, beta_zero);
+    k_gemm_small<T><<<blocks, 256, 0, s>>>(L.small_tasks.p, L.n_small, L.terms.p, b, beta_zero,
+                                           active);
     DMRG_LAUNCHED();
   }
   if (L.n_tiles) {
     k_gemm_tiled<T><<<int(L.n_tiles), 256, 0, s>>>(L.tiles.p, L.large_tasks.p, L.terms.p, b,
-                                                   beta_zero);
+                                                   beta_zero, active);
     DMRG_LAUNCHED();
   }
 }
-template void run_gemm_tasks<double>(const DevTaskList&, const Bases<double>&, int, cudaStream_t);
-template void run_gemm_tasks<float>(const DevTaskList&, const Bases<float>&, int, cudaStream_t);
+template void run_gemm_tasks<double>(const DevTaskList&, const Bases<double>&, int, cudaStream_t,
+                                     const int32_t*);
+template void run_gemm_tasks<float>(const DevTaskList&, const Bases<float>&, int, cudaStream_t,
+                                    const int32_t*);
 
 // ------------------------------------------------------------------------------------
 // copy tasks (one warp per destination sub-block)

@@ -62,15 +62,27 @@ def test_rejects_invalid_problems(lib):
     assert _bad(lib, p, dav_max_sub=2) == lib.DMRG_EINVAL
 
 
-def test_operator_partition_counts_match_oracle(lib):
-    """The library's host-side operator partition has as many products per bond as the
-    oracle's (both prune structurally zero labels): checked through the layout-free
-    create path on a shuffled order."""
+@pytest.mark.parametrize("space,Np,Nn,seed", [("sd", 2, 2, 1), ("p", 2, 3, 4), ("pf", 4, 4, 2)])
+def test_operator_partition_counts_match_oracle(lib, space, Np, Nn, seed):
+    """The library's host-side operator partition has, at every bond, exactly as many
+    operator products as the oracle's (both prune labels that cannot connect the vacuum to
+    the full Hamiltonian), on a shuffled chain order: the number of superblock terms the
+    paper's two-block Hamiltonian sums over."""
     from oracle.hamiltonian import ChainHamiltonian
     from oracle.mpo import MPO
-    p = make_problem("sd", 2, 2, 0, seed=1)
-    rng = np.random.default_rng(0)
+    p = make_problem(space, Np, Nn, (Np + Nn) % 2, seed=seed)
+    rng = np.random.default_rng(seed)
     p = p.with_order(rng.permutation(p.n_sites))
     d = lib.DMRG(p)     # validates and builds the partition; no device work
+    m = MPO(ChainHamiltonian(p))
+    got = [d.partition_terms(b) for b in range(p.n_sites - 1)]
+    ref = [m.n_terms(b) for b in range(p.n_sites - 1)]
     d.close()
-    assert MPO(ChainHamiltonian(p)).n_terms(11) > 0
+    assert got == ref
+    assert max(got) > 2 * p.n_sites     # pair operators appear in the middle
+    with pytest.raises(lib.DmrgError):
+        d2 = lib.DMRG(p)
+        try:
+            d2.partition_terms(p.n_sites - 1)
+        finally:
+            d2.close()

@@ -1,0 +1,95 @@
+"""GPU parity on the pf 4p+4n workload (40 m-scheme sites, 4p+4n, 2M = 0, m-scheme
+dimension 1,963,461, seed 2), chain order = the Fiedler order of the mutual information of
+the exact ground state, through the C-ABI in FP64.
+
+Stored expected values (tests/golden/c2_pf4p4n.json, written by tests/golden/make_c2.py from
+oracle/ only): the exact ground-state energy by the oracle's Lanczos, the frozen order, and
+every step of two oracle sweeps at M = 256 from the seeded starting state (Davidson
+tolerance 1e-10 on both sides).
+
+* Two sweeps at M = 256: every step's energy within 1e-8 MeV of the oracle's, the truncation
+  errors within 1e-10 and the kept states per sector of every new block bit-exact.  The
+  Davidson product counts are reported, not compared: these steps take 20-70 products with
+  thick restarts, and the reduction orders of the two sides move the step at which the
+  residual crosses 1e-8 by a product or two without changing the converged energy.
+* The schedule 256(4) -> 512(4) -> 1024(4) from the same start: sweep energies above the
+  exact energy (variational, 1e-9), non-increasing from one M to the next, and the last one
+  within 0.5 MeV of the exact energy.
+"""
+import dataclasses
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gen import make_problem, initial_mps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_pf4p4n.json")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1507_00161_gb300.build import build
+    build()
+    import paper_1507_00161_gb300 as P
+    assert torch.cuda.is_available()
+    return P
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _problem(g):
+    prob = make_problem("pf", 4, 4, 0, seed=2)
+    return dataclasses.replace(prob, order=np.array(g["order"], dtype=np.int32))
+
+
+def test_c2_sweeps_match_oracle(P, golden):
+    prob = _problem(golden)
+    M = golden["dmrg"]["M"]
+    d = P.DMRG(prob, dav_tol=golden["dmrg"]["dav_tol"])
+    d.build_blocks(initial_mps(prob, M, golden["dmrg"]["mps_seed"]))
+    N = prob.n_sites
+    seq = [(p, 0) for p in range(1, N - 2)] + [(p, 1) for p in range(N - 3, 0, -1)]
+    worst, dprod = 0.0, 0
+    for sw in golden["dmrg"]["sweeps"]:
+        assert len(sw["steps"]) == len(seq)
+        for (p, dr), ref in zip(seq, sw["steps"]):
+            st = d.step(p, dr, M)
+            assert (ref["p"], ref["dir"]) == (p, dr)
+            worst = max(worst, abs(st["energy"] - ref["energy"]))
+            assert abs(st["energy"] - ref["energy"]) <= 1e-8, (p, dr)
+            dprod = max(dprod, abs(st["n_products"] - ref["n_products"]))
+            assert abs(st["trunc_err"] - ref["trunc_err"]) <= 1e-10, (p, dr)
+            qn, dims = d.block_sectors(dr, p)
+            kept = sorted([list(map(int, q)) + [int(m)] for q, m in zip(qn, dims) if m])
+            assert kept == ref["kept"], (p, dr)
+    d.close()
+    print("[C2] worst step energy difference vs oracle: %.2e MeV; largest difference in "
+          "Davidson products: %d" % (worst, dprod))
+
+
+def test_c2_schedule_approaches_exact(P, golden):
+    prob = _problem(golden)
+    e_exact = golden["exact"]["energy"]
+    d = P.DMRG(prob)
+    d.build_blocks(initial_mps(prob, 256, golden["dmrg"]["mps_seed"]))
+    last = {}
+    for M in (256, 512, 1024):
+        for _ in range(4):
+            _, e = d.sweep(M)
+            assert e >= e_exact - 1e-9
+        last[M] = e
+    d.close()
+    assert last[512] <= last[256] + 1e-9
+    assert last[1024] <= last[512] + 1e-9
+    assert last[1024] - e_exact <= 0.5
+    print("[C2] sweep energies at M = 256, 512, 1024: %s; exact %.10f MeV" %
+          ([round(last[m], 8) for m in (256, 512, 1024)], e_exact))
