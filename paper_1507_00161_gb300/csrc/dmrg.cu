@@ -159,7 +159,8 @@ struct Super {
   // of its terms above 32): two grouped GEMM passes, T_k = psi(b_in) R_k^T into a scratch,
   // then psi'(b_out) = sum_k s_k L_k T_k (every such output block written by one task)
   DevTaskList big1, big2;
-  int64_t big_t_elems = 0;
+  DevBuf<HeffRed> big_red;            // partial blocks of stage-2 term groups, added in order
+  int64_t big_t_elems = 0, big_p_elems = 0, n_big_red = 0;
   int64_t n_big_blocks = 0;
   struct Term {
     int64_t lb, rb;
@@ -235,7 +236,8 @@ struct dmrg_ctx {
   int svd_cluster = 0;         // forced cluster size of the truncation SVDs (0: per sector)
   int64_t eig_noconv = 0;      // truncations with such an SVD
   dmrg::DevBuf<float> f32a, f32b, f32T, part32;
-  dmrg::DevBuf<double> part64, xpad64, ybat64;
+  dmrg::DevBuf<double> part64, xpad64, ybat64, bigpart64;
+  dmrg::DevBuf<float> bigpart32;  // partial blocks of the stage-2 term groups
   dmrg::DevBuf<float> xpad32;
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
@@ -1232,31 +1234,70 @@ static void build_super(Ctx& c, int p) {
     sb->p_elems = pelems;
   }
   {
-    // grouped GEMM passes of the big output blocks
+    // grouped GEMM passes of the big output blocks.  Stage 2 sums over every term of an
+    // output block (K = sum of the terms' d_Li, tens of thousands at M = 4096), so the terms
+    // are cut into groups of at most kBigGroupK inner elements: each group writes a partial
+    // block, and the partial blocks are added in group order afterwards (deterministic)
+    constexpr int64_t kBigGroupK = 2048;
     TaskList g1, g2;
-    int64_t toff2 = 0;
+    std::vector<HeffRed> red2;
+    int64_t toff2 = 0, poff2 = 0;
     for (int bo = 0; bo < nb; ++bo) {
       if (!big_bo[bo]) continue;
       ++sb->n_big_blocks;
       const int dLo = sb->bdl[bo], dRo = sb->bdr[bo];
-      g2.begin_task(Operand{sb->boff[bo], B_Y, dRo}, dLo, dRo);
+      const int64_t mn = int64_t(dLo) * dRo;
+      // groups of terms
+      std::vector<int64_t> gstart(1, i_beg[bo]);
+      int64_t kacc = 0;
       for (int64_t j = i_beg[bo]; j < i_beg[bo + 1]; ++j) {
-        const Super::Term& tm = sb->terms_host[j];
-        const int dLi = sb->bdl[tm.bin], dRi = sb->bdr[tm.bin];
-        g1.begin_task(Operand{toff2, B_T, dRo}, dLi, dRo);
-        g1.add_term(Operand{sb->pad_off[tm.bin], B_X, dRi},
-                    Operand{sb->R.blocks[tm.rb].off, B_ROPS, dRi}, dRi, 2, 1.0);
-        g2.add_term(Operand{sb->L.blocks[tm.lb].off, B_LOPS, dLi}, Operand{toff2, B_T, dRo}, dLi,
-                    0, tm.sign);
-        toff2 += int64_t(dLi) * dRo;
+        const int dLi = sb->bdl[sb->terms_host[j].bin];
+        if (kacc > 0 && kacc + dLi > kBigGroupK) {
+          gstart.push_back(j);
+          kacc = 0;
+        }
+        kacc += dLi;
+      }
+      gstart.push_back(i_beg[bo + 1]);
+      const int groups = int(gstart.size()) - 1;
+      for (int g = 0; g < groups; ++g) {
+        if (groups == 1) g2.begin_task(Operand{sb->boff[bo], B_Y, dRo}, dLo, dRo);
+        else g2.begin_task(Operand{poff2 + g * mn, B_Z, dRo}, dLo, dRo);
+        for (int64_t j = gstart[g]; j < gstart[g + 1]; ++j) {
+          const Super::Term& tm = sb->terms_host[j];
+          const int dLi = sb->bdl[tm.bin], dRi = sb->bdr[tm.bin];
+          g1.begin_task(Operand{toff2, B_T, dRo}, dLi, dRo);
+          g1.add_term(Operand{sb->pad_off[tm.bin], B_X, dRi},
+                      Operand{sb->R.blocks[tm.rb].off, B_ROPS, dRi}, dRi, 2, 1.0);
+          g2.add_term(Operand{sb->L.blocks[tm.lb].off, B_LOPS, dLi}, Operand{toff2, B_T, dRo},
+                      dLi, 0, tm.sign);
+          toff2 += int64_t(dLi) * dRo;
+        }
+      }
+      if (groups > 1) {
+        HeffRed r;
+        r.yoff = sb->boff[bo];
+        r.poff = poff2;
+        r.ld = dRo;
+        r.r0 = 0;
+        r.c0 = 0;
+        r.m = dLo;
+        r.n = dRo;
+        r.groups = groups;
+        r.inst = 0;
+        r.pad = 0;
+        red2.push_back(r);
+        poff2 += int64_t(groups) * mn;
       }
     }
     sb->big_t_elems = toff2;
+    sb->big_p_elems = poff2;
     if (sb->n_big_blocks) {
       int64_t be[NBASE] = {0};
       be[B_X] = sb->pad_size;
       be[B_Y] = sb->size;
       be[B_T] = std::max<int64_t>(toff2, 1);
+      be[B_Z] = std::max<int64_t>(poff2, 1);
       be[B_LOPS] = sb->L.n_elems;
       be[B_ROPS] = sb->R.n_elems;
       // the tensor-core engine takes every task as tiles; the FP64 one runs small tasks
@@ -1264,6 +1305,8 @@ static void build_super(Ctx& c, int p) {
       const int64_t lim = c.opt.precision == DMRG_FP64 ? 1024 : 0;
       sb->big1.build(g1, be, c.stream, lim);
       sb->big2.build(g2, be, c.stream, lim);
+      sb->big_red.upload(red2, c.stream);
+      sb->n_big_red = int64_t(red2.size());
     }
   }
   lap(2);
@@ -1363,14 +1406,20 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st)
                        st);
     if (sb.n_big_blocks) {
       c.T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      c.bigpart64.alloc(std::max<int64_t>(sb.big_p_elems, 1));
       Bases<double> bb{};
       bb.p[B_LOPS] = sb.L.data.p;
       bb.p[B_ROPS] = sb.R.data.p;
       bb.p[B_X] = c.xpad64.p;
       bb.p[B_Y] = y;
       bb.p[B_T] = c.T.p;
+      bb.p[B_Z] = c.bigpart64.p;
       run_gemm_tasks<double>(sb.big1, bb, 1, st);
       run_gemm_tasks<double>(sb.big2, bb, 1, st);
+      HeffPtrs<double> rp{};
+      rp.Y[0] = y;
+      rp.P[0] = c.bigpart64.p;
+      heff_reduce<double>(sb.big_red.p, sb.n_big_red, rp, st);
     }
   } else {
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
@@ -1387,14 +1436,20 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st)
     heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, st);
     if (sb.n_big_blocks) {
       c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      c.bigpart32.alloc(std::max<int64_t>(sb.big_p_elems, 1));
       Bases<void> bb{};
       bb.p[B_LOPS] = sb.L.data32.p;
       bb.p[B_ROPS] = sb.R.data32.p;
       bb.p[B_X] = c.xpad32.p;
       bb.p[B_Y] = c.f32b.p;
       bb.p[B_T] = c.f32T.p;
+      bb.p[B_Z] = c.bigpart32.p;
       run_gemm_tasks_tc<float, float, float>(sb.big1, bb, 1, st);
       run_gemm_tasks_tc<float, float, float>(sb.big2, bb, 1, st);
+      HeffPtrs<float> rp{};
+      rp.Y[0] = c.f32b.p;
+      rp.P[0] = c.bigpart32.p;
+      heff_reduce<float>(sb.big_red.p, sb.n_big_red, rp, st);
     }
     to_f64(c.f32b.p, y, sb.size, st);
   }
@@ -3126,8 +3181,14 @@ static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
       bb.p[B_X] = c.xpad64.p;
       bb.p[B_Y] = c.ybat64.p;
       bb.p[B_T] = c.T.p;
+      bb.p[B_Z] = c.bigpart64.p;
       run_gemm_tasks<double>(sb.big1, bb, 1, B.bs, act + i);
       run_gemm_tasks<double>(sb.big2, bb, 1, B.bs, act + i);
+      HeffPtrs<double> rp{};
+      rp.Y[0] = c.ybat64.p;
+      rp.P[0] = c.bigpart64.p;
+      rp.active = act + i;
+      heff_reduce<double>(sb.big_red.p, sb.n_big_red, rp, B.bs);
     }
     for (int i : inst) {
       Ctx& c = *B.ctx[i];
@@ -3159,8 +3220,14 @@ static void batch_issue(dmrg_batch& B, const std::vector<int>& inst) {
       bb.p[B_X] = c.xpad32.p;
       bb.p[B_Y] = c.f32b.p;
       bb.p[B_T] = c.f32T.p;
+      bb.p[B_Z] = c.bigpart32.p;
       run_gemm_tasks_tc<float, float, float>(sb.big1, bb, 1, B.bs, act + i);
       run_gemm_tasks_tc<float, float, float>(sb.big2, bb, 1, B.bs, act + i);
+      HeffPtrs<float> rp{};
+      rp.Y[0] = c.f32b.p;
+      rp.P[0] = c.bigpart32.p;
+      rp.active = act + i;
+      heff_reduce<float>(sb.big_red.p, sb.n_big_red, rp, B.bs);
     }
     for (int i : inst) {
       Ctx& c = *B.ctx[i];
@@ -3179,12 +3246,18 @@ static void batch_buffers(dmrg_batch& B, const std::vector<int>& inst) {
       c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
       c.xpad64.alloc(sb.pad_size);
       c.ybat64.alloc(std::max<int64_t>(sb.size, 1));
-      if (sb.n_big_blocks) c.T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      if (sb.n_big_blocks) {
+        c.T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+        c.bigpart64.alloc(std::max<int64_t>(sb.big_p_elems, 1));
+      }
     } else {
       c.f32b.alloc(std::max<int64_t>(sb.size, 1));
       c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
       c.xpad32.alloc(sb.pad_size);
-      if (sb.n_big_blocks) c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      if (sb.n_big_blocks) {
+        c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+        c.bigpart32.alloc(std::max<int64_t>(sb.big_p_elems, 1));
+      }
     }
   }
 }

@@ -130,7 +130,7 @@ __device__ __forceinline__ void store_chunk(const Chunk& ch, int ta, int tb, uin
 }
 
 template <class TA, class TB, class TC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_gemm_tc(const GemmTile* __restrict__ tiles, const GemmTask* __restrict__ tasks,
               const GemmTerm* __restrict__ terms, Bases<void> b, int beta_zero,
               const int32_t* __restrict__ active) {
