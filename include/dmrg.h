@@ -67,7 +67,7 @@ typedef struct {
 
 typedef struct {
   int32_t precision;        /* DMRG_FP64 or DMRG_MIXED_FP32                            */
-  int32_t reserved0;        /* preconditioner: DMRG_PRECOND_DIAG or DMRG_PRECOND_MLP   */
+  int32_t precond;          /* preconditioner: DMRG_PRECOND_DIAG or DMRG_PRECOND_MLP   */
   double dav_tol;           /* Davidson residual-norm tolerance (MeV), e.g. 1e-8       */
   int32_t dav_max_iter;     /* maximum H_eff products per step, e.g. 100               */
   int32_t dav_max_sub;      /* subspace size before thick restart, 4..64, e.g. 24      */
@@ -320,7 +320,10 @@ int dmrg_block_sectors(dmrg_ctx* ctx, int32_t side, int32_t b, int32_t* n, int32
  * called.  A product that needs more intermediate storage is rejected with DMRG_EINVAL
  * and a message giving the size it needs.
  *   Preconditions: the superblock at p must already be set up by an allocating call at
- * the same position (dmrg_psi_layout or dmrg_heff_apply); otherwise DMRG_EINVAL.
+ * the same position (dmrg_psi_layout or dmrg_heff_apply; they prepare this entry point's
+ * task lists only for products that fit the array); otherwise DMRG_EINVAL.  The device the
+ * context was created on must be current (DMRG_EINVAL otherwise): the array's address is
+ * looked up on the current device.
  *   First call on a device: it looks up the array's device address (once per device,
  * with that device current; with lazy module loading the driver loads the code that
  * holds the array at that moment); make that first call before any stream capture.

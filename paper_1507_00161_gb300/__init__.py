@@ -52,7 +52,7 @@ class Problem(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+    _fields_ = [("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("dav_tol", ctypes.c_double), ("dav_max_iter", ctypes.c_int32),
                 ("dav_max_sub", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 

@@ -556,6 +556,9 @@ void mlp_err_vec(const double* x, const double* psi, const double* sc, int64_t n
 
 // read-only view of the H_eff task lists of the superblock currently set up at position p
 // (nothing is built or allocated; false if the superblock at p is not set up)
+// elements of the allocation-free product's file-scope intermediate (noalloc.cu): 2^21
+// doubles = 16 MiB; the two-stage lists it needs are built only for superblocks that fit
+constexpr int64_t kScratchElems = int64_t(1) << 21;
 struct HeffView {
   const DevTaskList* st1;
   const DevTaskList* st2;
@@ -564,6 +567,8 @@ struct HeffView {
   int64_t size;
   int64_t t_elems;
   cudaStream_t stream;
+  int device;               // the device the context was created on
+  bool lists_ready;         // the two-stage lists exist (only when t_elems <= kScratchElems)
 };
 bool heff_view(dmrg_ctx* c, int p, HeffView* v);
 void set_error(dmrg_ctx* c, const char* msg);

@@ -211,6 +211,7 @@ struct dmrg_ctx {
   double dbss_target = 0.0;  // and the discarded-weight target
   cudaStream_t stream = nullptr;
   int N = 0;
+  int device = -1;             // the device current when the context was created
   std::vector<std::set<std::tuple<int, int, int>>> reach_left, reach_right;
   std::vector<dmrg::Blk> left, right;
   bool built = false;
@@ -1355,7 +1356,8 @@ static Super& super_at(Ctx& c, int p) {
 // two-stage H_eff lists (T = psi R^T, then psi' = sum s L T) used by the allocation-free
 // entry point; built by the allocating ABI calls only
 static void ensure_two_stage(Ctx& c, Super& sb) {
-  if (sb.two_stage_ready) return;
+  // only superblocks whose intermediate fits the allocation-free product's array need them
+  if (sb.two_stage_ready || sb.t_elems > kScratchElems) return;
   TaskList s1, s2;
   int64_t toff = 0;
   int last_out = -1;
@@ -1651,7 +1653,7 @@ static void dav_begin(Ctx& c, Super& sb, const double* guess, double* out, DavRu
   ensure_ws(c, R.n, R.sub);
   ensure_diag(c, sb);
   R.ld = c.ws_n;
-  R.use_mlp = c.opt.reserved0 == DMRG_PRECOND_MLP && c.mlp_trained && R.nroots == 1;
+  R.use_mlp = c.opt.precond == DMRG_PRECOND_MLP && c.mlp_trained && R.nroots == 1;
   if (c.mlp_harvest) {
     c.hist_x.alloc(kHist * R.ld);
     c.hist_r.alloc(kHist * R.ld);
@@ -2406,7 +2408,7 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st,
 }
 
 bool heff_view(dmrg_ctx* c, int p, HeffView* v) {
-  if (!c || !c->sb || c->sb->p != p || !c->sb->two_stage_ready) return false;
+  if (!c || !c->sb || c->sb->p != p) return false;
   Super& sb = *c->sb;
   v->st1 = &sb.st1;
   v->st2 = &sb.st2;
@@ -2415,6 +2417,8 @@ bool heff_view(dmrg_ctx* c, int p, HeffView* v) {
   v->size = sb.size;
   v->t_elems = sb.t_elems;
   v->stream = c->stream;
+  v->device = c->device;
+  v->lists_ready = sb.two_stage_ready;
   return true;
 }
 
@@ -2482,6 +2486,10 @@ extern "C" int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dm
                      opt->dav_max_sub <= 64,
                  DMRG_EINVAL, "bad Davidson options");
     c->stream = static_cast<cudaStream_t>(opt->stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {   // no device here: host-only use
+      c->device = -1;
+      (void)cudaGetLastError();
+    }
     build_chain(prob, c->chain);
     build_mpo(c->chain, c->mpo);
     c->N = c->chain.N;
@@ -2754,7 +2762,7 @@ extern "C" int dmrg_set_roots(dmrg_ctx* c, int32_t n_roots) {
   return guarded(c, [&] {
     DMRG_REQUIRE(n_roots == 1 || n_roots == 2, DMRG_EINVAL, "n_roots must be 1 or 2");
     DMRG_REQUIRE(n_roots == 1 || (c->opt.precision == DMRG_FP64 &&
-                                  c->opt.reserved0 == DMRG_PRECOND_DIAG),
+                                  c->opt.precond == DMRG_PRECOND_DIAG),
                  DMRG_EINVAL, "two-state targeting needs DMRG_FP64 and the diagonal preconditioner");
     if (n_roots != c->n_roots) c->psi1_valid = false;
     c->n_roots = n_roots;
@@ -2837,7 +2845,7 @@ extern "C" int dmrg_set_options(dmrg_ctx* c, const dmrg_options* opt) {
                      opt->dav_max_sub <= 64,
                  DMRG_EINVAL, "bad Davidson options");
     DMRG_REQUIRE(c->n_roots == 1 || (opt->precision == DMRG_FP64 &&
-                                     opt->reserved0 == DMRG_PRECOND_DIAG),
+                                     opt->precond == DMRG_PRECOND_DIAG),
                  DMRG_EINVAL, "two-state targeting needs DMRG_FP64 and the diagonal preconditioner");
     const bool prec_changed = opt->precision != c->opt.precision;
     // byte counts, FP32 operator shadows and product lists depend on the precision

@@ -6,13 +6,17 @@
 // prefetch of up to four terms per warp), but both small products of a term run as warp
 // matrix multiply-accumulates m16n8k8 on TF32 operands split into high and low parts:
 //     a b  ~  a_hi b_hi + a_hi b_lo + a_lo b_hi   (three MMAs, FP32 accumulation)
-// which keeps FP32-level accuracy (the dropped a_lo b_lo term is ~2^-22 relative).  The
-// sector blocks are about 8 x 8 (tens at most), far below the 64-row minimum of a
-// CTA-level tcgen05 MMA, so the warp-level instruction is the one that fits them.
+// which keeps FP32-level accuracy (the dropped a_lo b_lo term is ~2^-22 relative).  This
+// kernel takes the output blocks up to the big-block edge (dmrg_set_tuning): in the first
+// sweeps from a random start they are a few states wide, well below the 64-row minimum of
+// a CTA-level MMA, so the warp-level instruction is the one that fits them; wider blocks
+// (hundreds of states in converged sweeps at M = 4096) go to the grouped GEMM passes of
+// tgemm.cu.
 //     X (dLi x n)  = psi (dLi x dRi) R^T        (M = dLi, N = n, K = dRi)
 //     Y (m x n)   += s L (m x dLi) X             (M = m,   N = n, K = dLi)
-// Terms with an inner dimension above 32 are processed in 32-wide chunks staged
-// synchronously.  Deterministic: fixed term order per warp, fixed warp and group order.
+// Terms with an inner dimension above 32 are processed in 32-wide chunks staged by
+// asynchronous copies (the L chunk in flight while the psi and R chunks load).
+// Deterministic: fixed term order per warp, fixed warp and group order.
 #include <stdint.h>
 
 #include <mutex>

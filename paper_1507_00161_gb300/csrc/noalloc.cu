@@ -13,9 +13,9 @@
 
 namespace {
 
-// 2,097,152 doubles = 16 MiB, held by every GPU that loads the library until exit
-constexpr int64_t kScratchElems = int64_t(1) << 21;
-static __device__ __align__(256) double g_heff_scratch[kScratchElems];
+// 2,097,152 doubles = 16 MiB (kScratchElems, common.h), held by every GPU that loads the
+// library until exit
+static __device__ __align__(256) double g_heff_scratch[dmrg::kScratchElems];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -50,10 +50,18 @@ extern "C" int dmrg_heff_apply_noalloc(dmrg_ctx* c, int32_t p, const double* x, 
     DMRG_REQUIRE(dmrg::heff_view(c, p, &v), DMRG_EINVAL,
                  "the superblock at this position is not set up: call dmrg_psi_layout or "
                  "dmrg_heff_apply at this position first (those calls allocate)");
-    DMRG_REQUIRE(v.t_elems <= kScratchElems, DMRG_EINVAL,
+    DMRG_REQUIRE(v.t_elems <= dmrg::kScratchElems, DMRG_EINVAL,
                  "this product needs " + std::to_string(v.t_elems) +
                      " doubles of intermediate storage; the allocation-free entry point is "
                      "limited to 2097152 doubles (16 MiB)");
+    DMRG_REQUIRE(v.lists_ready, DMRG_EINVAL,
+                 "the superblock at this position is not set up: call dmrg_psi_layout or "
+                 "dmrg_heff_apply at this position first (those calls allocate)");
+    int dev = -1;
+    DMRG_CUDA(cudaGetDevice(&dev));
+    DMRG_REQUIRE(v.device < 0 || dev == v.device, DMRG_EINVAL,
+                 "the current device is not the one the context was created on; make it "
+                 "current before this call");
     double* T = scratch_on_current_device();
     // every element of the intermediate is written by stage 1 before stage 2 reads it;
     // the output is cleared here because blocks without terms receive no stage-2 task

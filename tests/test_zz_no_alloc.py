@@ -32,7 +32,7 @@ def test_noalloc_matches_heff_apply(space, Np, Nn, seed, M0):
         ref_h = ref.cpu().numpy()
         ys = [torch.empty_like(x) for _ in range(3)]
         torch.cuda.synchronize()
-        free0 = None
+        free0 = mallocs0 = None
         for i, y in enumerate(ys):        # calls in a row, output pre-filled with NaN
             if i == 1:
                 # the first call on a device is the documented set-up (address lookup;
@@ -40,6 +40,7 @@ def test_noalloc_matches_heff_apply(space, Np, Nn, seed, M0):
                 # checked over the calls after it
                 torch.cuda.synchronize()
                 free0 = torch.cuda.mem_get_info()[0]
+                mallocs0 = d.counters()["pool_mallocs"]
             y.fill_(float("nan"))
             d.heff_apply_noalloc(p, x, y)
             yh = y.cpu().numpy()
@@ -47,9 +48,38 @@ def test_noalloc_matches_heff_apply(space, Np, Nn, seed, M0):
             assert err <= 1e-12, err
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0
+        assert d.counters()["pool_mallocs"] == mallocs0   # no allocation by the library
+
+
+def test_noalloc_rejects_products_above_its_limit():
+    """A product whose intermediate exceeds the 2,097,152-double array is rejected with
+    DMRG_EINVAL and leaves the output untouched (pf 8p+8n mid-chain after sweeps at 512
+    and 1024 states)."""
+    from paper_1507_00161_gb300.build import build
+    build()
+    import paper_1507_00161_gb300 as P
+    prob = make_problem("pf", 8, 8, 0, seed=3)
+    d = P.DMRG(prob, precision=P.MIXED_FP32)
+    d.build_blocks(initial_mps(prob, 512, 3003))
+    d.sweep(512)
+    d.sweep(1024)
+    for p in range(1, 19):
+        d.step(p, 0, 1024)
+    d.set_options(precision=P.FP64)
+    size = d.psi_layout(19)["size"]
+    x = torch.ones(size, dtype=torch.float64, device="cuda")
+    y = torch.full_like(x, float("nan"))
+    with pytest.raises(P.DmrgError) as e:
+        d.heff_apply_noalloc(19, x, y)
+    assert e.value.code == P.DMRG_EINVAL
+    assert "2097152" in str(e.value)
+    assert torch.isnan(y).all()
+    d.close()
 
 
 def test_noalloc_requires_set_up_superblock():
+    from paper_1507_00161_gb300.build import build
+    build()
     import paper_1507_00161_gb300 as P
     prob = make_problem("p", 2, 2, 0, seed=12)
     d = P.DMRG(prob)
