@@ -1112,7 +1112,8 @@ static void build_super(Ctx& c, int p) {
         const int cls = dmax <= 8 ? 0 : dmax <= 16 ? 1 : dmax <= 32 ? 2 : 3;
         hist[cls] += 1.0;
         hist[4 + cls] += std::min(f1, f2);
-        kfl += f1;   // the tile kernels form psi R^T first
+        // the tile kernels form psi R^T first; the grouped passes take the cheaper order
+        kfl += big_bo[bo] ? std::min(f1, f2) : f1;
         sb->terms_host[j] = Super::Term{it.lb, it.rb, it.bin, it.bout, it.sign};
       }
       bo_flops[bo] = fl;
@@ -1235,8 +1236,10 @@ static void build_super(Ctx& c, int p) {
     sb->p_elems = pelems;
   }
   {
-    // grouped GEMM passes of the big output blocks.  Stage 2 sums over every term of an
-    // output block (K = sum of the terms' d_Li, tens of thousands at M = 4096), so the terms
+    // grouped GEMM passes of the big output blocks, each term in its cheaper association:
+    // T = psi R^T then s L T, or Z = L psi then s Z R^T (both kinds of terms may share a
+    // stage-2 task).  Stage 2 sums over every term of an output block (K = sum of the
+    // terms' inner dimensions, tens of thousands at M = 4096), so the terms
     // are cut into groups of at most kBigGroupK inner elements: each group writes a partial
     // block, and the partial blocks are added in group order afterwards (deterministic)
     constexpr int64_t kBigGroupK = 2048;
@@ -1252,12 +1255,15 @@ static void build_super(Ctx& c, int p) {
       std::vector<int64_t> gstart(1, i_beg[bo]);
       int64_t kacc = 0;
       for (int64_t j = i_beg[bo]; j < i_beg[bo + 1]; ++j) {
-        const int dLi = sb->bdl[sb->terms_host[j].bin];
-        if (kacc > 0 && kacc + dLi > kBigGroupK) {
+        const int dLi = sb->bdl[sb->terms_host[j].bin], dRi = sb->bdr[sb->terms_host[j].bin];
+        const double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;
+        const double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;
+        const int kk = f1 <= f2 ? dLi : dRi;   // the inner dimension of its stage-2 term
+        if (kacc > 0 && kacc + kk > kBigGroupK) {
           gstart.push_back(j);
           kacc = 0;
         }
-        kacc += dLi;
+        kacc += kk;
       }
       gstart.push_back(i_beg[bo + 1]);
       const int groups = int(gstart.size()) - 1;
@@ -1267,12 +1273,26 @@ static void build_super(Ctx& c, int p) {
         for (int64_t j = gstart[g]; j < gstart[g + 1]; ++j) {
           const Super::Term& tm = sb->terms_host[j];
           const int dLi = sb->bdl[tm.bin], dRi = sb->bdr[tm.bin];
-          g1.begin_task(Operand{toff2, B_T, dRo}, dLi, dRo);
-          g1.add_term(Operand{sb->pad_off[tm.bin], B_X, dRi},
-                      Operand{sb->R.blocks[tm.rb].off, B_ROPS, dRi}, dRi, 2, 1.0);
-          g2.add_term(Operand{sb->L.blocks[tm.lb].off, B_LOPS, dLi}, Operand{toff2, B_T, dRo},
-                      dLi, 0, tm.sign);
-          toff2 += int64_t(dLi) * dRo;
+          // the cheaper association of L psi R^T for this term
+          const double f1 = 2.0 * dLi * dRi * dRo + 2.0 * dLo * dLi * dRo;   // psi R^T first
+          const double f2 = 2.0 * dLo * dLi * dRi + 2.0 * dLo * dRi * dRo;   // L psi first
+          if (f1 <= f2) {
+            // T = psi R^T (d_Li x d_Ro), then psi' += s L T
+            g1.begin_task(Operand{toff2, B_T, dRo}, dLi, dRo);
+            g1.add_term(Operand{sb->pad_off[tm.bin], B_X, dRi},
+                        Operand{sb->R.blocks[tm.rb].off, B_ROPS, dRi}, dRi, 2, 1.0);
+            g2.add_term(Operand{sb->L.blocks[tm.lb].off, B_LOPS, dLi},
+                        Operand{toff2, B_T, dRo}, dLi, 0, tm.sign);
+            toff2 += int64_t(dLi) * dRo;
+          } else {
+            // Z = L psi (d_Lo x d_Ri), then psi' += s Z R^T
+            g1.begin_task(Operand{toff2, B_T, dRi}, dLo, dRi);
+            g1.add_term(Operand{sb->L.blocks[tm.lb].off, B_LOPS, dLi},
+                        Operand{sb->pad_off[tm.bin], B_X, dRi}, dLi, 0, 1.0);
+            g2.add_term(Operand{toff2, B_T, dRi}, Operand{sb->R.blocks[tm.rb].off, B_ROPS, dRi},
+                        dRi, 2, tm.sign);
+            toff2 += int64_t(dLo) * dRi;
+          }
         }
       }
       if (groups > 1) {

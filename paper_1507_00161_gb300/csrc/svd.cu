@@ -45,7 +45,6 @@ namespace dmrg {
 
 namespace {
 
-constexpr int kSvdThreads = 256;
 constexpr int kMaxSweeps = 40;
 constexpr size_t kSvdSmemMax = 226 * 1024;   // dynamic share; the static part needs a little
 
@@ -93,7 +92,10 @@ __device__ __forceinline__ void round_pair(int m, int r, int k, int& p, int& q) 
   q = max(a, b);
 }
 
-__global__ void __launch_bounds__(kSvdThreads, 1)
+// NT threads per CTA: 256 in clusters (large sectors), 64 for sectors of one CTA, whose
+// rounds are short and barrier-bound, so that several fit on an SM
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 64 ? 4 : 1)
     k_svd_jacobi(const SvdJob* __restrict__ jobs, const double* __restrict__ psi0,
                  const double* __restrict__ psi1, double* __restrict__ w_out,
                  double* __restrict__ vs_out, int* __restrict__ noconv, double tol_scale) {
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
   const int rank = int(cl.block_rank());
   const SvdJob jb = jobs[blockIdx.x / C];
   const SvdShape S = svd_shape(jb, C);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = kSvdThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
   const int ld = S.cols + 1;   // odd leading dimension: fewer bank conflicts across rows
   // shared layout: A rows, V rows, partials [2][3 P] (also used for final norms and signs),
   // rotations [2 P], pair indices
@@ -119,11 +121,11 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
   const int nr = max(0, r1 - r0);
   const int v0 = rank * S.Rv, v1 = min(S.d, v0 + S.Rv);
   const int nv = max(0, v1 - v0);
-  for (int e = tid; e < nr * S.cols; e += kSvdThreads) {
+  for (int e = tid; e < nr * S.cols; e += NT) {
     const int r = e / S.cols, c = e - r * S.cols;
     A[r * ld + c] = S.needV ? b_at(jb, psi0, psi1, c, r0 + r) : b_at(jb, psi0, psi1, r0 + r, c);
   }
-  for (int e = tid; e < nv * S.cols; e += kSvdThreads) {
+  for (int e = tid; e < nv * S.cols; e += NT) {
     const int r = e / S.cols, c = e - r * S.cols;
     V[r * ld + c] = (v0 + r == c) ? 1.0 : 0.0;
   }
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
       }
       cl.sync();
       // 2. cluster sums in rank order and the rotations (identical in every CTA)
-      for (int k = tid; k < m / 2; k += kSvdThreads) {
+      for (int k = tid; k < m / 2; k += NT) {
         int p, q;
         round_pair(m, r, k, p, q);
         double al = 0.0, be = 0.0, ga = 0.0;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
       __syncthreads();
       // 3. rotate the local rows of A and V
       const int half = m / 2;
-      for (int e = tid; e < half * nr; e += kSvdThreads) {
+      for (int e = tid; e < half * nr; e += NT) {
         const int k = e / nr, i = e - k * nr;
         const double sn = rot[2 * k + 1];
         if (sn == 0.0) continue;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
         A[i * ld + p] = cs * x - sn * y;
         A[i * ld + q] = sn * x + cs * y;
       }
-      for (int e = tid; e < half * nv; e += kSvdThreads) {
+      for (int e = tid; e < half * nv; e += NT) {
         const int k = e / nv, i = e - k * nv;
         const double sn = rot[2 * k + 1];
         if (sn == 0.0) continue;
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
   }
   cl.sync();
   double* nrm = rot;   // reuse: cols norms (rot holds 2 P >= cols entries)
-  for (int c = tid; c < S.cols; c += kSvdThreads) {
+  for (int c = tid; c < S.cols; c += NT) {
     double al = 0.0;
     for (int k = 0; k < C; ++k) al += cl.map_shared_rank(pb, k)[c];
     nrm[c] = al;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
   __syncthreads();
   // rank of each column: descending weight, ties by index
   int* order = pq;   // order[c] = output position of column c
-  for (int c = tid; c < S.cols; c += kSvdThreads) {
+  for (int c = tid; c < S.cols; c += NT) {
     const double wc = nrm[c];
     int pos = 0;
     for (int j = 0; j < S.cols; ++j) {
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
   cl.sync();
   double* sgn = pb;   // own norms buffer is no longer read by anyone after the next barrier
   __syncthreads();
-  for (int c = tid; c < S.cols; c += kSvdThreads) {
+  for (int c = tid; c < S.cols; c += NT) {
     double bv = -1.0, bi = 1e300;
     for (int k = 0; k < C; ++k) {
       const double* rp = cl.map_shared_rank(pc, k);
@@ -300,17 +302,17 @@ __global__ void __launch_bounds__(kSvdThreads, 1)
   __syncthreads();
   // outputs: eigenvalues (rank 0) and the eigenvector rows this CTA holds
   if (rank == 0)
-    for (int c = tid; c < S.d; c += kSvdThreads)
+    for (int c = tid; c < S.d; c += NT)
       w_out[jb.w_off + c] = 0.0;
   __syncthreads();
   if (rank == 0)
-    for (int c = tid; c < S.cols; c += kSvdThreads) w_out[jb.w_off + order[c]] = nrm[c];
-  for (int e = tid; e < nu * S.d; e += kSvdThreads) {
+    for (int c = tid; c < S.cols; c += NT) w_out[jb.w_off + order[c]] = nrm[c];
+  for (int e = tid; e < nu * S.d; e += NT) {
     const int i = e / S.d, c = e - i * S.d;   // row i of U (global row u0 + i), output column c
     vs_out[jb.vs_off + int64_t(u0 + i) * S.d + c] = 0.0;
   }
   __syncthreads();
-  for (int e = tid; e < nu * S.cols; e += kSvdThreads) {
+  for (int e = tid; e < nu * S.cols; e += NT) {
     const int i = e / S.cols, c = e - i * S.cols;
     double v = U[i * ld + c] * sgn[2 * c];
     if (!S.needV) v = nrm[c] > 0.0 ? v / sqrt(nrm[c]) : 0.0;
@@ -340,15 +342,17 @@ void svd_jacobi(const SvdJob* d_jobs, int n_jobs, int C, size_t smem, const doub
   if (n_jobs <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
-    DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(kSvdSmemMax)));
-    DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                   1));
+    DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi<256>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSvdSmemMax)));
+    DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi<256>,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi<64>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSvdSmemMax)));
   });
   DMRG_REQUIRE(smem <= kSvdSmemMax, DMRG_EINVAL, "internal: SVD job exceeds shared memory");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(n_jobs) * unsigned(C), 1, 1);
-  cfg.blockDim = dim3(kSvdThreads, 1, 1);
+  cfg.blockDim = dim3(C == 1 ? 64 : 256, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -358,8 +362,12 @@ void svd_jacobi(const SvdJob* d_jobs, int n_jobs, int C, size_t smem, const doub
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  DMRG_CUDA(cudaLaunchKernelEx(&cfg, k_svd_jacobi, d_jobs, psi0, psi1, w, vs, d_noconv,
-                               2.220446049250313e-16));
+  if (C == 1)
+    DMRG_CUDA(cudaLaunchKernelEx(&cfg, k_svd_jacobi<64>, d_jobs, psi0, psi1, w, vs, d_noconv,
+                                 2.220446049250313e-16));
+  else
+    DMRG_CUDA(cudaLaunchKernelEx(&cfg, k_svd_jacobi<256>, d_jobs, psi0, psi1, w, vs, d_noconv,
+                                 2.220446049250313e-16));
   DMRG_LAUNCHED();
 }
 
