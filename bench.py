@@ -46,7 +46,7 @@ WORKLOAD_NAME = ("pf-shell 40 sites, 8p+8n, M_z=0 (m-scheme dim 1,087,455,228), 
                  "4096(4), then two-site steps at M=4096 centred on the middle of the chain")
 # the oracle's sample of the same workload: its H_eff products at position 1 with the
 # starting state's right blocks at M0 states (building those blocks is not timed)
-CPU_SAMPLE_M0 = 512
+CPU_SAMPLE_M0 = 256
 
 
 def _peaks():
