@@ -476,6 +476,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t_job = time.perf_counter() - t_job0
         job_flops = sum(x["heff_flops"] for x in sweeps)
+        # work split of the product tuned on the middle superblock at the final M
+        tuned_edge, tune_ms = d.autotune(N // 2, reps=2)
         # ---- timed two-site steps at the final M, centred on the middle of the chain
         setup, warm, timed = _timed_window(N, args.steps, args.warmup)
         for (p, dr) in setup + warm:
@@ -605,6 +607,8 @@ def run_gpu(args):
         "config": {"workload": wname, "M": M,
                    "positions": "%d..%d left to right" % (timed[0][0], timed[-1][0]),
                    "schedule": "+".join("%d(%d)" % x for x in schedule),
+                   "autotune": {"heff_big_edge": tuned_edge,
+                                "ms_by_edge": {str(k): round(v, 3) for k, v in tune_ms.items()}},
                    "precision": "FP32 contractions (split-TF32 tensor cores), FP64 "
                                 "Davidson/SVD/energy",
                    "parallelism": "replicas" if world > 1 else "single GPU",

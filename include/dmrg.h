@@ -386,6 +386,19 @@ typedef struct {
 int dmrg_set_tuning(dmrg_ctx* ctx, const dmrg_tuning* t);
 int dmrg_get_tuning(dmrg_ctx* ctx, dmrg_tuning* t);
 
+/* Autotuner of the product's work split (dmrg_tuning.heff_big_edge), on the superblock at
+ * position p (not in the paper): one H_eff product is timed for each candidate edge (0 =
+ * fused tile kernels only, then 32, 64, 128, 256) with CUDA events on the context stream,
+ * best of reps >= 1 after one untimed product; the fastest is kept, and within 5 % of it
+ * the smallest positive edge (its grouped passes sum their products with compensation and
+ * are the more accurate).  The edge is set as by dmrg_set_tuning; the products agree to
+ * rounding whichever is chosen, but the choice follows measured times.  chosen: the edge
+ * set; edges, ms (optional host arrays of 5): the candidates and their best times.  Call
+ * between steps (the superblock held by the context is dropped).  DMRG_EINVAL for a
+ * position whose blocks are not available or reps < 1. */
+int dmrg_autotune(dmrg_ctx* ctx, int32_t p, int32_t reps, int32_t* chosen, int32_t* edges,
+                  double* ms);
+
 /* Number of operator products L_k (x) R_k across bond b (0 <= b <= N-2) of the normal /
  * complementary operator partition built at dmrg_create: the terms the superblock
  * Hamiltonian sums over when the cut lies at bond b (labels that cannot connect the vacuum

@@ -26,6 +26,7 @@ EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks
             "dmrg_psi_layout", "dmrg_heff_apply", "dmrg_davidson",
             "dmrg_truncate_renormalize", "dmrg_step", "dmrg_sweep", "dmrg_block_sectors",
             "dmrg_rdm_eigh", "dmrg_set_tuning", "dmrg_get_tuning", "dmrg_partition_terms",
+            "dmrg_autotune",
             "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_dot_rdm",
             "dmrg_get_counters",
             "dmrg_heff_cost",
@@ -141,6 +142,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_rdm_eigh": [P, i32, i32, i32, P, P, P, P, P, P],
         "dmrg_set_tuning": [P, ctypes.POINTER(Tuning)],
         "dmrg_partition_terms": [P, i32, P],
+        "dmrg_autotune": [P, i32, i32, P, P, P],
         "dmrg_get_tuning": [P, ctypes.POINTER(Tuning)],
         "dmrg_mlp_reset": [P, ctypes.c_uint64],
         "dmrg_mlp_harvest": [P, i32, i32],
@@ -285,6 +287,16 @@ class DMRG:
         n = ctypes.c_int32()
         self._check(self.lib.dmrg_partition_terms(self.h, int(b), ctypes.byref(n)))
         return n.value
+
+    def autotune(self, p, reps=2):
+        """Time the product's work split on the superblock at p and keep the fastest
+        (dmrg_autotune): (chosen edge, {edge: best ms})."""
+        ch = ctypes.c_int32()
+        edges = np.zeros(5, dtype=np.int32)
+        ms = np.zeros(5)
+        self._check(self.lib.dmrg_autotune(self.h, int(p), int(reps), ctypes.byref(ch),
+                                           _np_ptr(edges), _np_ptr(ms)))
+        return ch.value, {int(e): float(t) for e, t in zip(edges, ms)}
 
     def tuning(self):
         t = Tuning()

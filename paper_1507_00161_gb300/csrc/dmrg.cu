@@ -2889,6 +2889,65 @@ extern "C" int dmrg_set_tuning(dmrg_ctx* c, const dmrg_tuning* t) {
   });
 }
 
+extern "C" int dmrg_autotune(dmrg_ctx* c, int32_t p, int32_t reps, int32_t* chosen,
+                             int32_t* edges, double* ms) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(reps >= 1, DMRG_EINVAL, "reps must be at least 1");
+    static const int kCand[5] = {0, 32, 64, 128, 256};
+    double best_ms[5];
+    const int keep = c->big_edge;
+    cudaEvent_t e0, e1;
+    DMRG_CUDA(cudaEventCreate(&e0));
+    DMRG_CUDA(cudaEventCreate(&e1));
+    try {
+      for (int i = 0; i < 5; ++i) {
+        c->big_edge = kCand[i];
+        drop_superblock(*c);
+        Super& sb = super_at(*c, p);
+        DevBuf<double> x, y;
+        x.alloc(std::max<int64_t>(sb.size, 1));
+        y.alloc(std::max<int64_t>(sb.size, 1));
+        fill_value(x.p, sb.size, 1.0 / std::sqrt(double(std::max<int64_t>(sb.size, 1))),
+                   c->stream);
+        heff(*c, sb, x.p, y.p, c->stream);   // untimed: first use of the lists and buffers
+        double bt = 1e300;
+        for (int r = 0; r < reps; ++r) {
+          DMRG_CUDA(cudaEventRecord(e0, c->stream));
+          heff(*c, sb, x.p, y.p, c->stream);
+          DMRG_CUDA(cudaEventRecord(e1, c->stream));
+          DMRG_CUDA(cudaEventSynchronize(e1));
+          float t = 0.f;
+          DMRG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+          bt = std::min(bt, double(t));
+        }
+        best_ms[i] = bt;
+      }
+    } catch (...) {
+      c->big_edge = keep;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int pick = 0;
+    for (int i = 1; i < 5; ++i)
+      if (best_ms[i] < best_ms[pick]) pick = i;
+    for (int i = 1; i < 5; ++i)   // the smallest positive edge within 5 % of the fastest
+      if (best_ms[i] <= 1.05 * best_ms[pick]) {
+        pick = i;
+        break;
+      }
+    c->big_edge = kCand[pick];
+    drop_superblock(*c);
+    if (chosen) *chosen = kCand[pick];
+    for (int i = 0; i < 5; ++i) {
+      if (edges) edges[i] = kCand[i];
+      if (ms) ms[i] = best_ms[i];
+    }
+  });
+}
+
 extern "C" int dmrg_get_tuning(dmrg_ctx* c, dmrg_tuning* t) {
   return guarded(c, [&] {
     DMRG_REQUIRE(t != nullptr, DMRG_EINVAL, "NULL tuning");

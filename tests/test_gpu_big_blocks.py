@@ -135,3 +135,27 @@ def test_tuning_rejects_bad_values(P):
     d.set_tuning(heff_big_edge=48, svd_cluster=8)
     assert d.tuning() == {"heff_big_edge": 48, "svd_cluster": 8}
     d.close()
+
+
+def test_autotune_picks_a_candidate_and_products_agree(P):
+    """The autotuner times the work splits on a mid-chain superblock, keeps one of the
+    candidates, and the product with the chosen split equals the FP64 product (2e-6 with
+    the grouped passes, 1e-5 with the fused kernels only)."""
+    prob, d = _mid_chain(P, precision=P.MIXED_FP32)
+    p = 19
+    chosen, times = d.autotune(p, reps=2)
+    assert chosen in (0, 32, 64, 128, 256)
+    assert set(times) == {0, 32, 64, 128, 256} and all(t > 0 for t in times.values())
+    assert d.tuning()["heff_big_edge"] == chosen
+    n = d.psi_layout(p)["size"]
+    x = torch.tensor(np.random.default_rng(5).standard_normal(n), dtype=torch.float64,
+                     device="cuda")
+    y = torch.empty_like(x)
+    d.heff_apply(p, x, y)
+    d.set_options(precision=P.FP64)
+    ref = torch.empty_like(x)
+    d.heff_apply(p, x, ref)
+    err = float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref))
+    assert err <= (1e-5 if chosen == 0 else 2e-6), (chosen, err)
+    print("[autotune] chosen edge %d, times (ms) %s" % (chosen, times))
+    d.close()
