@@ -92,10 +92,10 @@ __device__ __forceinline__ void round_pair(int m, int r, int k, int& p, int& q) 
   q = max(a, b);
 }
 
-// NT threads per CTA: 256 in clusters (large sectors), 64 for sectors of one CTA, whose
-// rounds are short and barrier-bound, so that several fit on an SM
+// NT threads per CTA (256; 64 for single-CTA sectors was measured slower: their rounds are
+// latency-bound, and fewer threads lengthen each round more than the shorter barriers save)
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 64 ? 4 : 1)
+__global__ void __launch_bounds__(NT, 1)
     k_svd_jacobi(const SvdJob* __restrict__ jobs, const double* __restrict__ psi0,
                  const double* __restrict__ psi1, double* __restrict__ w_out,
                  double* __restrict__ vs_out, int* __restrict__ noconv, double tol_scale) {
@@ -346,13 +346,11 @@ void svd_jacobi(const SvdJob* d_jobs, int n_jobs, int C, size_t smem, const doub
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSvdSmemMax)));
     DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi<256>,
                                    cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    DMRG_CUDA(cudaFuncSetAttribute(k_svd_jacobi<64>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSvdSmemMax)));
   });
   DMRG_REQUIRE(smem <= kSvdSmemMax, DMRG_EINVAL, "internal: SVD job exceeds shared memory");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(n_jobs) * unsigned(C), 1, 1);
-  cfg.blockDim = dim3(C == 1 ? 64 : 256, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -362,12 +360,8 @@ void svd_jacobi(const SvdJob* d_jobs, int n_jobs, int C, size_t smem, const doub
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (C == 1)
-    DMRG_CUDA(cudaLaunchKernelEx(&cfg, k_svd_jacobi<64>, d_jobs, psi0, psi1, w, vs, d_noconv,
-                                 2.220446049250313e-16));
-  else
-    DMRG_CUDA(cudaLaunchKernelEx(&cfg, k_svd_jacobi<256>, d_jobs, psi0, psi1, w, vs, d_noconv,
-                                 2.220446049250313e-16));
+  DMRG_CUDA(cudaLaunchKernelEx(&cfg, k_svd_jacobi<256>, d_jobs, psi0, psi1, w, vs, d_noconv,
+                               2.220446049250313e-16));
   DMRG_LAUNCHED();
 }
 
