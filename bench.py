@@ -47,6 +47,12 @@ WORKLOAD_NAME = ("pf-shell 40 sites, 8p+8n, M_z=0 (m-scheme dim 1,087,455,228), 
 # the oracle's sample of the same workload: its H_eff products at position 1 with the
 # starting state's right blocks at M0 states (building those blocks is not timed)
 CPU_SAMPLE_M0 = 256
+# DRAM bytes (read + write, ncu dram__bytes_read/write.sum) of the mixed product's kernels
+# per algorithmic byte: 137.4 MB against 91.5 MB per product on pf 8p+8n at M = 1024,
+# position 19, with the grouped passes on every block wider than 32 states (the headline
+# superblock is too large for a multi-pass capture; the excess is the intermediate of the
+# two-stage passes, which grows with the product); re-take it when the kernels change
+HEFF_TRAFFIC_PER_BYTE = 137.4 / 91.5
 
 
 def _peaks():
@@ -622,7 +628,8 @@ def run_gpu(args):
                     "fp64_energy": fp64["sweeps"][-1]["energy"] if fp64.get("sweeps") else None},
         "fp64": {k: fp64.get(k) for k in ("heff_tflops", "dE_mixed_vs_fp64", "position")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": HEFF_TRAFFIC_PER_BYTE * heff_bytes / max(nprod, 1),
                      "kernel": "mixed H_eff product (its kernels between CUDA events on the "
                                "context stream)", "peak_kind": peak_kind},
         "cpu_baseline": cpu,
