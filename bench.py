@@ -650,6 +650,55 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small case of the product's kernels for multi-pass ncu captures: pf 8p+8n (seed 3,
+    mixed path), sweeps of the schedule up to --M, steps 1..18 left to right at --M, the
+    grouped passes on every block wider than --profile-edge states, then inside the profiler
+    range either one H_eff product at position 19 ('product') or the two-site step there
+    ('step').  Prints one JSON line describing the case."""
+    import numpy as np
+    import torch
+    from paper_1507_00161_gb300.build import build
+    build()
+    import paper_1507_00161_gb300 as P
+    from gen import make_problem, initial_mps
+    w = WORKLOAD
+    M = args.M
+    prob = make_problem(w["space"], w["Np"], w["Nn"], w["two_Mz"], seed=w["seed"])
+    d = P.DMRG(prob, precision=P.MIXED_FP32)
+    d.build_blocks(initial_mps(prob, SCHEDULE[0][0], w["mps_seed"]))
+    for m, _ in SCHEDULE:
+        if m > M:
+            break
+        d.sweep(m)
+    p = 19
+    for q in range(1, p):
+        d.step(q, 0, M)
+    d.set_tuning(heff_big_edge=args.profile_edge)
+    n = d.psi_layout(p)["size"]
+    flops, nbytes, _ = d.heff_cost(p)
+    x = torch.tensor(np.random.default_rng(1).standard_normal(n), dtype=torch.float64,
+                     device="cuda")
+    y = torch.empty_like(x)
+    d.heff_apply(p, x, y)
+    torch.cuda.synchronize()
+    free_b, total_b = torch.cuda.mem_get_info()
+    torch.cuda.profiler.start()
+    out = {"profile_case": args.profile_case, "M": M, "position": p, "psi_size": n,
+           "heff_gflop": flops / 1e9, "heff_mb": nbytes / 1e6,
+           "device_mem_gb": round((total_b - free_b) / 1e9, 2)}
+    if args.profile_case == "product":
+        d.heff_apply(p, x, y)
+    else:
+        st = d.step(p, 0, M)
+        out.update(n_products=st["n_products"], kept=st["kept"])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    d.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -674,11 +723,17 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")
+    ap.add_argument("--profile-case", choices=["product", "step"], default=None,
+                    help="run only the small capture case at --M (see run_profile_case)")
+    ap.add_argument("--profile-edge", type=int, default=32,
+                    help="grouped-pass edge of the capture case")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_gpu(args)
 
 
