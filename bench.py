@@ -380,6 +380,89 @@ def run_next_rows(P, prob, init, M, e_fixed):
     return out
 
 
+PFG_SCHEDULE = [(512, 1), (1024, 2), (2048, 1)]
+
+
+def run_pfg(P, M_max):
+    """The pf+g9/2 workload: 60 m-scheme sites, 12p+12n (m-scheme dimension 3.45e14),
+    random J-coupled two-body ensemble seed 4, for the targets 2M_z = 0 and 2M_z = 4, mixed
+    path, seeded starting state (M0 = 512, seed 4004), schedule 512(1) -> 1024(2) ->
+    2048(1) capped at M_max.  Per sweep: seconds (CUDA events), H_eff TFLOP/s on the device,
+    energy.  The learned preconditioner is trained on the 2M_z = 0 instance (samples
+    harvested during its M = 1024 sweeps) and evaluated on the held-out 2M_z = 4 instance:
+    Davidson from the uniform guess at the middle positions of its final block state, with
+    the diagonal and with the learned preconditioner."""
+    import numpy as np
+    import torch
+    from gen import make_problem, initial_mps
+    out = {"workload": "pf+g9/2 60 sites, 12p+12n, seed 4, mixed path, schedule %s" %
+                       "+".join("%d(%d)" % x for x in PFG_SCHEDULE if x[0] <= M_max)}
+    theta = None
+    for tmz in (0, 4):
+        prob = make_problem("pfg", 12, 12, tmz, seed=4)
+        init = initial_mps(prob, PFG_SCHEDULE[0][0], 4004)
+        d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8)
+        d.build_blocks(init)
+        sweeps = []
+        for (M, n) in PFG_SCHEDULE:
+            if M > M_max:
+                break
+            for _ in range(n):
+                harvest = tmz == 0 and M == 1024
+                if harvest:
+                    d.mlp_harvest(True, 2048)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st, e = d.sweep(M)
+                e1.record()
+                e1.synchronize()
+                if harvest:
+                    d.mlp_harvest(False)
+                fl = sum(x["heff_flops"] * x["n_products"] for x in st)
+                hs = sum(x["heff_seconds"] for x in st)
+                sweeps.append({"M": M, "s": e0.elapsed_time(e1) / 1e3, "energy": e,
+                               "products": sum(x["n_products"] for x in st),
+                               "heff_tflops": fl / max(hs, 1e-12) / 1e12,
+                               "max_step_gflop": max(x["heff_flops"] for x in st) / 1e9})
+        free_b, total_b = torch.cuda.mem_get_info()
+        res = {"sweeps": sweeps, "device_mem_gb": round((total_b - free_b) / 1e9, 2)}
+        N = prob.n_sites
+        if tmz == 0:
+            d.mlp_reset(3)
+            t0 = time.perf_counter()
+            loss, ns = d.mlp_train(epochs=20, batch=1024, lr=1e-3, seed=4)
+            res["mlp"] = {"samples": ns, "loss": loss, "train_s": time.perf_counter() - t0}
+            theta = d.mlp_params()
+        elif theta is not None:
+            # held-out evaluation: the network trained on the 2M_z = 0 instance; the left-to-
+            # right half of a sweep at the final M, Davidson from the uniform guess at every
+            # fourth position with each preconditioner, then the step itself
+            d.mlp_set_params(theta)
+            M = sweeps[-1]["M"]
+            n_diag = n_mlp = 0
+            dmax = 0.0
+            for p in range(1, N - 2):
+                if p % 4 == 0:
+                    size = d.psi_layout(p)["size"]
+                    x0 = torch.ones(size, dtype=torch.float64, device="cuda")
+                    d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
+                    ea, sa = d.davidson(p, guess=x0, allow_noconv=True)
+                    d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_MLP)
+                    eb, sb = d.davidson(p, guess=x0, allow_noconv=True)
+                    d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
+                    n_diag += sa["n_products"]
+                    n_mlp += sb["n_products"]
+                    dmax = max(dmax, abs(ea - eb))
+                d.step(p, 0, M)
+            res["precond_held_out"] = {"positions": "every fourth of 1..%d at M=%d" % (N - 3, M),
+                                       "products_diagonal": n_diag, "products_learned": n_mlp,
+                                       "max_dE": dmax}
+        d.close()
+        out["two_Mz_%d" % tmz] = res
+    return out
+
+
 def max_over_ranks(x, dist=None):
     """The largest value of x over the ranks of the process group (x on a single rank)."""
     if dist is None:
@@ -598,6 +681,13 @@ def run_gpu(args):
         nr = run_next_rows(P, prob, init, M, None)
         if rank == 0:
             _emit("next_rows", nr)
+    if args.pfg_mmax > 0:
+        try:
+            pfg = run_pfg(P, args.pfg_mmax)
+        except Exception as exc:      # a side measurement never takes the bench line down
+            pfg = {"error": str(exc)}
+        if rank == 0:
+            _emit("pfg", pfg)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -718,6 +808,8 @@ def main():
                     help="learned vs diagonal preconditioner comparison (0: skip)")
     ap.add_argument("--next-rows", type=int, default=1,
                     help="also time a DBSS sweep and a two-state sweep (side measurements)")
+    ap.add_argument("--pfg-mmax", type=int, default=2048,
+                    help="largest M of the pf+g9/2 12p+12n side measurement (0: skip)")
     ap.add_argument("--workload", default="",
                     help="space:Np:Nn:seed of another system (profiling of smaller cases)")
     ap.add_argument("--profile-range", action="store_true",

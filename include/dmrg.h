@@ -137,7 +137,8 @@ typedef struct {
    * [18] Davidson: waits after each product, [19] Davidson iterations (a count),
    * [20] truncation sectors too large for the cluster SVD, decomposed from the explicit
    * density matrix instead (a count), [21] truncations whose SVD stopped at its sweep
-   * limit (a count), [22..23] reserved */
+   * limit (a count), [22] H_eff products replayed from a CUDA graph (a count),
+   * [23] reserved */
   double t_detail[24];
   int64_t pool_mallocs;     /* device allocations that missed the caching pool          */
   int64_t sb_small_tiles;   /* last superblock: tiles of the small-block product kernel */
@@ -364,8 +365,8 @@ int dmrg_mlp_loss_grad(dmrg_ctx* ctx, int32_t precision, const double* params, c
                        const double* T, int64_t B, double* loss, double* grad);
 int64_t dmrg_mlp_n_params(void);
 
-/* Work split of the kernels (not in the paper; results agree to rounding whatever the
- * split, which the tests check).
+/* Work split and launch mode of the kernels (not in the paper; results agree to rounding
+ * whatever the split, and bit for bit whatever the launch mode, which the tests check).
  *   heff_big_edge: an output block of H_eff psi whose own dimensions or whose terms' input
  *     dimensions exceed this edge is computed by two grouped GEMM passes (T_k = psi R_k^T
  *     into a device scratch, then psi' = sum_k s_k L_k T_k; split-TF32 tensor cores in
@@ -376,12 +377,19 @@ int64_t dmrg_mlp_n_params(void);
  *     are faster).
  *   svd_cluster: thread-block cluster size of the truncation's SVDs: 0 = chosen per sector
  *     (default), or 1, 8 or 16 for every sector whose shared-memory share fits.
+ *   heff_graph: 1 (default) = the kernels of the product that follow the staging of psi
+ *     are captured as a CUDA graph at the second product of a precision on a superblock
+ *     and replayed for every later product there (Davidson iterations, dmrg_heff_apply);
+ *     0 = every kernel launched eagerly.  The FP64 energy of the mixed path (one product
+ *     per step) is always eager.
  * Call between steps: the superblock held by the context is dropped and rebuilt at its next
  * use (a wave function held for truncation must be recomputed).  DMRG_EINVAL for values
- * out of range (heff_big_edge < 0 or > 4096, svd_cluster not 0, 1, 8 or 16). */
+ * out of range (heff_big_edge < 0 or > 4096, svd_cluster not 0, 1, 8 or 16, heff_graph not
+ * 0 or 1). */
 typedef struct {
   int32_t heff_big_edge;
   int32_t svd_cluster;
+  int32_t heff_graph;
 } dmrg_tuning;
 int dmrg_set_tuning(dmrg_ctx* ctx, const dmrg_tuning* t);
 int dmrg_get_tuning(dmrg_ctx* ctx, dmrg_tuning* t);

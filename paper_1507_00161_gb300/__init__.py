@@ -84,7 +84,8 @@ class StepStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("heff_big_edge", ctypes.c_int32), ("svd_cluster", ctypes.c_int32)]
+    _fields_ = [("heff_big_edge", ctypes.c_int32), ("svd_cluster", ctypes.c_int32),
+                ("heff_graph", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -301,13 +302,16 @@ class DMRG:
     def tuning(self):
         t = Tuning()
         self._check(self.lib.dmrg_get_tuning(self.h, ctypes.byref(t)))
-        return {"heff_big_edge": t.heff_big_edge, "svd_cluster": t.svd_cluster}
+        return {"heff_big_edge": t.heff_big_edge, "svd_cluster": t.svd_cluster,
+                "heff_graph": t.heff_graph}
 
-    def set_tuning(self, heff_big_edge=None, svd_cluster=None):
-        """Work split of the kernels (dmrg_set_tuning); None keeps the current value."""
+    def set_tuning(self, heff_big_edge=None, svd_cluster=None, heff_graph=None):
+        """Work split and launch mode of the kernels (dmrg_set_tuning); None keeps the
+        current value."""
         cur = self.tuning()
         t = Tuning(int(cur["heff_big_edge"] if heff_big_edge is None else heff_big_edge),
-                   int(cur["svd_cluster"] if svd_cluster is None else svd_cluster))
+                   int(cur["svd_cluster"] if svd_cluster is None else svd_cluster),
+                   int(cur["heff_graph"] if heff_graph is None else heff_graph))
         self._check(self.lib.dmrg_set_tuning(self.h, ctypes.byref(t)))
 
     def rdm_eigh(self, p, direction, cluster=0, vectors=True):

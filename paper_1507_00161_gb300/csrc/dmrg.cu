@@ -189,6 +189,22 @@ struct Super {
   int n_dtasks = 0;
   DevBuf<double> diag;
   bool diag_ready = false;
+  // the product's kernels after the staging of psi, captured as a CUDA graph at the second
+  // product of a precision (0 = FP64, 1 = mixed) on this superblock and replayed after that
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t n_launches = 0;       // kernel nodes
+    int64_t eager = 0, replays = 0;
+    const void* key[6] = {};      // scratch pointers at capture
+  } graph[2];
+  Super() = default;
+  Super(const Super&) = delete;
+  Super& operator=(const Super&) = delete;
+  ~Super() {
+    // an executable graph still in flight is released when it completes
+    for (auto& g : graph)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+  }
 };
 
 }  // namespace dmrg
@@ -237,7 +253,10 @@ struct dmrg_ctx {
   int svd_cluster = 0;         // forced cluster size of the truncation SVDs (0: per sector)
   int64_t eig_noconv = 0;      // truncations with such an SVD
   dmrg::DevBuf<float> f32a, f32b, f32T, part32;
-  dmrg::DevBuf<double> part64, xpad64, ybat64, bigpart64;
+  dmrg::DevBuf<double> part64, xpad64, ybat64, bigpart64, ygraph64;
+  int heff_graph = 1;          // replay the product as a CUDA graph (0: eager launches)
+  int64_t graph_replays = 0;   // products replayed from a graph
+  cudaStream_t cap_stream = nullptr;   // graph capture
   dmrg::DevBuf<float> bigpart32;  // partial blocks of the stage-2 term groups
   dmrg::DevBuf<float> xpad32;
   // precomputed per-site W entry orders (grouped by destination label)
@@ -287,6 +306,7 @@ struct dmrg_ctx {
     if (rq_out) cudaEventDestroy(rq_out);
     for (auto e : ev) cudaEventDestroy(e);
     if (h_words) cudaFreeHost(h_words);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 };
 
@@ -1408,46 +1428,60 @@ static void ensure_two_stage(Ctx& c, Super& sb) {
   sb.two_stage_ready = true;
 }
 
-static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st) {
-  // every psi' element is written by exactly one fused tile or one grouped-GEMM task of the
-  // big output blocks (blocks without terms get zero-term tiles or tasks), so no clearing
-  // pass is needed
-  const int nb = int(sb.bL.size());
-  if (c.opt.precision == DMRG_FP64) {
+// scratch of the product for one precision (0 = FP64, 1 = mixed), allocated before any launch
+// (and before a graph capture, which may not allocate)
+static void heff_buffers(Ctx& c, Super& sb, int prec) {
+  if (prec == 0) {
     c.part64.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad64.alloc(sb.pad_size);
-    pad_psi<double>(x, c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, st);
-    HeffPtrs<double> ptr{};
-    ptr.L[0] = sb.L.data.p;
-    ptr.R[0] = sb.R.data.p;
-    ptr.X[0] = c.xpad64.p;
-    ptr.Y[0] = y;
-    ptr.P[0] = c.part64.p;
-    heff_small<double>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
-    heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr,
-                       st);
+    c.ygraph64.alloc(std::max<int64_t>(sb.size, 1));
     if (sb.n_big_blocks) {
       c.T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
       c.bigpart64.alloc(std::max<int64_t>(sb.big_p_elems, 1));
-      Bases<double> bb{};
-      bb.p[B_LOPS] = sb.L.data.p;
-      bb.p[B_ROPS] = sb.R.data.p;
-      bb.p[B_X] = c.xpad64.p;
-      bb.p[B_Y] = y;
-      bb.p[B_T] = c.T.p;
-      bb.p[B_Z] = c.bigpart64.p;
-      run_gemm_tasks<double>(sb.big1, bb, 1, st);
-      run_gemm_tasks<double>(sb.big2, bb, 1, st);
-      HeffPtrs<double> rp{};
-      rp.Y[0] = y;
-      rp.P[0] = c.bigpart64.p;
-      heff_reduce<double>(sb.big_red.p, sb.n_big_red, rp, st);
     }
   } else {
     c.f32b.alloc(std::max<int64_t>(sb.size, 1));
     c.part32.alloc(std::max<int64_t>(sb.p_elems, 1));
     c.xpad32.alloc(sb.pad_size);
-    pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, st);
+    if (sb.n_big_blocks) {
+      c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
+      c.bigpart32.alloc(std::max<int64_t>(sb.big_p_elems, 1));
+    }
+  }
+}
+
+// the product's kernels after the staging of psi: small blocks, fused tiles, grouped passes
+// of the big output blocks and their reductions.  FP64 writes psi' to y64; the mixed path to
+// the FP32 buffer c.f32b.  Every psi' element is written by exactly one fused tile or one
+// grouped-GEMM task (blocks without terms get zero-term tiles or tasks), so no clearing pass
+// is needed.
+static void heff_core(Ctx& c, Super& sb, int prec, double* y64, cudaStream_t st) {
+  if (prec == 0) {
+    HeffPtrs<double> ptr{};
+    ptr.L[0] = sb.L.data.p;
+    ptr.R[0] = sb.R.data.p;
+    ptr.X[0] = c.xpad64.p;
+    ptr.Y[0] = y64;
+    ptr.P[0] = c.part64.p;
+    heff_small<double>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
+    heff_fused<double>(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr,
+                       st);
+    if (sb.n_big_blocks) {
+      Bases<double> bb{};
+      bb.p[B_LOPS] = sb.L.data.p;
+      bb.p[B_ROPS] = sb.R.data.p;
+      bb.p[B_X] = c.xpad64.p;
+      bb.p[B_Y] = y64;
+      bb.p[B_T] = c.T.p;
+      bb.p[B_Z] = c.bigpart64.p;
+      run_gemm_tasks<double>(sb.big1, bb, 1, st);
+      run_gemm_tasks<double>(sb.big2, bb, 1, st);
+      HeffPtrs<double> rp{};
+      rp.Y[0] = y64;
+      rp.P[0] = c.bigpart64.p;
+      heff_reduce<double>(sb.big_red.p, sb.n_big_red, rp, st);
+    }
+  } else {
     HeffPtrs<float> ptr{};
     ptr.L[0] = sb.L.data32.p;
     ptr.R[0] = sb.R.data32.p;
@@ -1457,8 +1491,6 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st)
     heff_small<float>(sb.stiles.p, sb.n_stiles, sb.fitems.p, ptr, st);
     heff_tc(sb.ftiles.p, sb.n_ftiles, sb.fitems.p, sb.fred.p, sb.n_fred, ptr, st);
     if (sb.n_big_blocks) {
-      c.f32T.alloc(std::max<int64_t>(sb.big_t_elems, 1));
-      c.bigpart32.alloc(std::max<int64_t>(sb.big_p_elems, 1));
       Bases<void> bb{};
       bb.p[B_LOPS] = sb.L.data32.p;
       bb.p[B_ROPS] = sb.R.data32.p;
@@ -1473,8 +1505,85 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st)
       rp.P[0] = c.bigpart32.p;
       heff_reduce<float>(sb.big_red.p, sb.n_big_red, rp, st);
     }
-    to_f64(c.f32b.p, y, sb.size, st);
   }
+}
+
+// the scratch pointers a captured product reads and writes (a reallocation invalidates it)
+static void heff_graph_key(const Ctx& c, int prec, const void* (&k)[6]) {
+  if (prec == 0) {
+    const void* v[6] = {c.part64.p, c.xpad64.p, c.ygraph64.p, c.T.p, c.bigpart64.p, nullptr};
+    for (int i = 0; i < 6; ++i) k[i] = v[i];
+  } else {
+    const void* v[6] = {c.f32b.p, c.part32.p, c.xpad32.p, c.f32T.p, c.bigpart32.p, nullptr};
+    for (int i = 0; i < 6; ++i) k[i] = v[i];
+  }
+}
+
+// capture heff_core into the superblock's graph of this precision (on a private stream:
+// capture records launches without running them, and the context stream may be the legacy
+// default stream, which cannot be captured)
+static void heff_capture(Ctx& c, Super& sb, int prec) {
+  Super::Graph& G = sb.graph[prec];
+  if (!c.cap_stream) DMRG_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  DMRG_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    heff_core(c, sb, prec, c.ygraph64.p, c.cap_stream);
+  } catch (...) {
+    cudaStreamEndCapture(c.cap_stream, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  DMRG_CUDA(cudaStreamEndCapture(c.cap_stream, &g));
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  // the captured launches were counted by DMRG_LAUNCHED; they run at every replay instead
+  g_launches.fetch_sub(int64_t(n), std::memory_order_relaxed);
+  if (e == cudaSuccess && n > 0) e = cudaGraphInstantiate(&G.exec, g, 0);
+  cudaGraphDestroy(g);
+  DMRG_CUDA(e);
+  G.n_launches = int64_t(n);
+  heff_graph_key(c, prec, G.key);
+}
+
+static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st,
+                 bool graph_ok = true) {
+  const int prec = c.opt.precision == DMRG_FP64 ? 0 : 1;
+  const int nb = int(sb.bL.size());
+  heff_buffers(c, sb, prec);
+  if (prec == 0)
+    pad_psi<double>(x, c.xpad64.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, st);
+  else
+    pad_psi<float>(x, c.xpad32.p, sb.d_src_off.p, sb.d_pad_off.p, sb.d_pad_len.p, nb, st);
+  Super::Graph& G = sb.graph[prec];
+  bool replay = false;
+  if (graph_ok && c.heff_graph) {
+    if (G.exec) {
+      const void* k[6];
+      heff_graph_key(c, prec, k);
+      if (!std::equal(k, k + 6, G.key)) {   // scratch moved: capture again
+        DMRG_CUDA(cudaGraphExecDestroy(G.exec));
+        G.exec = nullptr;
+      }
+    }
+    // the first product of a precision runs eagerly (kernel attributes, first-use checks);
+    // from the second on the captured graph is replayed
+    if (!G.exec && G.eager >= 1) heff_capture(c, sb, prec);
+    replay = G.exec != nullptr;
+  }
+  if (replay) {
+    DMRG_CUDA(cudaGraphLaunch(G.exec, st));
+    g_launches.fetch_add(G.n_launches, std::memory_order_relaxed);
+    ++G.replays;
+    ++c.graph_replays;
+    if (prec == 0)
+      DMRG_CUDA(cudaMemcpyAsync(y, c.ygraph64.p, sizeof(double) * sb.size,
+                                cudaMemcpyDeviceToDevice, st));
+  } else {
+    heff_core(c, sb, prec, y, st);
+    ++G.eager;
+  }
+  if (prec == 1) to_f64(c.f32b.p, y, sb.size, st);
 }
 
 // H_eff product with its device time recorded (events resolved by resolve_heff_timing)
@@ -1522,7 +1631,7 @@ static void heff64(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t s
   int keep = c.opt.precision;
   c.opt.precision = DMRG_FP64;
   try {
-    heff(c, sb, x, y, st);
+    heff(c, sb, x, y, st, false);   // once per step: nothing to replay
   } catch (...) {
     c.opt.precision = keep;
     throw;
@@ -2883,8 +2992,11 @@ extern "C" int dmrg_set_tuning(dmrg_ctx* c, const dmrg_tuning* t) {
     DMRG_REQUIRE(t->svd_cluster == 0 || t->svd_cluster == 1 || t->svd_cluster == 8 ||
                      t->svd_cluster == 16,
                  DMRG_EINVAL, "svd_cluster must be 0, 1, 8 or 16");
+    DMRG_REQUIRE(t->heff_graph == 0 || t->heff_graph == 1, DMRG_EINVAL,
+                 "heff_graph must be 0 or 1");
     c->big_edge = t->heff_big_edge;
     c->svd_cluster = t->svd_cluster;
+    c->heff_graph = t->heff_graph;
     drop_superblock(*c);   // its product lists follow the old split: rebuilt at the next use
   });
 }
@@ -2953,6 +3065,7 @@ extern "C" int dmrg_get_tuning(dmrg_ctx* c, dmrg_tuning* t) {
     DMRG_REQUIRE(t != nullptr, DMRG_EINVAL, "NULL tuning");
     t->heff_big_edge = c->big_edge;
     t->svd_cluster = c->svd_cluster;
+    t->heff_graph = c->heff_graph;
   });
 }
 
@@ -2992,6 +3105,7 @@ extern "C" int dmrg_get_counters(dmrg_ctx* c, dmrg_counters* out) {
     for (int i = 0; i < 24; ++i) out->t_detail[i] = c->t_detail[i];
     out->t_detail[15] = 1e-9 * double(g_malloc_ns.load());
     out->t_detail[21] = double(c->eig_noconv);
+    out->t_detail[22] = double(c->graph_replays);
     out->pool_mallocs = g_malloc_count.load();
   });
 }

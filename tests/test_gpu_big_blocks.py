@@ -132,8 +132,11 @@ def test_tuning_rejects_bad_values(P):
         d.set_tuning(heff_big_edge=-1)
     with pytest.raises(P.DmrgError):
         d.set_tuning(svd_cluster=3)
-    d.set_tuning(heff_big_edge=48, svd_cluster=8)
-    assert d.tuning() == {"heff_big_edge": 48, "svd_cluster": 8}
+    with pytest.raises(P.DmrgError):
+        d.set_tuning(heff_graph=2)
+    assert d.tuning() == {"heff_big_edge": 128, "svd_cluster": 0, "heff_graph": 1}
+    d.set_tuning(heff_big_edge=48, svd_cluster=8, heff_graph=0)
+    assert d.tuning() == {"heff_big_edge": 48, "svd_cluster": 8, "heff_graph": 0}
     d.close()
 
 
@@ -159,3 +162,51 @@ def test_autotune_picks_a_candidate_and_products_agree(P):
     assert err <= 1e-5, (chosen, err)
     print("[autotune] chosen edge %d, times (ms) %s" % (chosen, times))
     d.close()
+
+
+def test_graph_replay_is_bit_exact(P):
+    """The product replayed from its CUDA graph (dmrg_tuning.heff_graph = 1: eager first
+    product, captured at the second) equals the eagerly launched product bit for bit, in
+    both precisions, on a superblock with fused tiles and grouped passes (pf 4p+4n, first
+    position of the M0 = 1024 starting state, grouped passes above 32 states); a sweep with
+    graphs gives the same energies, bit for bit, as one without."""
+    prob = make_problem("pf", 4, 4, 0, seed=2)
+    init = initial_mps(prob, 1024, 2002)
+    out = {}
+    for graph in (0, 1):
+        d = P.DMRG(prob)
+        d.build_blocks(init)
+        d.set_tuning(heff_big_edge=32, heff_graph=graph)
+        n = d.psi_layout(1)["size"]
+        x = torch.tensor(np.random.default_rng(3).standard_normal(n), dtype=torch.float64,
+                         device="cuda")
+        for prec in (P.FP64, P.MIXED_FP32):
+            d.set_options(precision=prec)
+            r0 = d.counters()["t_detail"][22]
+            ys = []
+            for _ in range(3):
+                y = torch.full_like(x, float("nan"))
+                d.heff_apply(1, x, y)
+                ys.append(y.cpu().numpy())
+            replays = d.counters()["t_detail"][22] - r0
+            assert replays == (2 if graph else 0), (graph, prec, replays)
+            out[(graph, prec)] = ys
+        d.close()
+    for prec in (P.FP64, P.MIXED_FP32):
+        ref = out[(0, prec)][0]
+        assert np.all(np.isfinite(ref))
+        for y in out[(0, prec)] + out[(1, prec)]:
+            assert np.array_equal(y, ref), prec
+    prob = make_problem("sd", 3, 3, 0, seed=1)
+    init = initial_mps(prob, 64, 9)
+    energies = {}
+    for graph in (0, 1):
+        d = P.DMRG(prob, precision=P.MIXED_FP32)
+        d.set_tuning(heff_graph=graph)
+        d.build_blocks(init)
+        steps, e = d.sweep(64)
+        energies[graph] = [s["energy"] for s in steps]
+        if graph:
+            assert d.counters()["t_detail"][22] > 0
+        d.close()
+    assert energies[0] == energies[1]
