@@ -195,6 +195,7 @@ struct Super {
     cudaGraphExec_t exec = nullptr;
     int64_t n_launches = 0;       // kernel nodes
     int64_t eager = 0, replays = 0;
+    bool empty = false;           // the product launches no kernel here
     const void* key[6] = {};      // scratch pointers at capture
   } graph[2];
   Super() = default;
@@ -1543,6 +1544,7 @@ static void heff_capture(Ctx& c, Super& sb, int prec) {
   cudaGraphDestroy(g);
   DMRG_CUDA(e);
   G.n_launches = int64_t(n);
+  G.empty = n == 0;   // nothing to replay: stay eager
   heff_graph_key(c, prec, G.key);
 }
 
@@ -1568,7 +1570,7 @@ static void heff(Ctx& c, Super& sb, const double* x, double* y, cudaStream_t st,
     }
     // the first product of a precision runs eagerly (kernel attributes, first-use checks);
     // from the second on the captured graph is replayed
-    if (!G.exec && G.eager >= 1) heff_capture(c, sb, prec);
+    if (!G.exec && !G.empty && G.eager >= 1) heff_capture(c, sb, prec);
     replay = G.exec != nullptr;
   }
   if (replay) {
