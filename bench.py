@@ -23,7 +23,8 @@ MeV, seed 3), single-particle energies U[0,4) MeV; seeded random starting state 
 * cpu_baseline: the FP64 oracle's H_eff products on the same workload (position 1), timed
   on the host cores in a child process.
 Side measurements (the schedule's sweeps, the timed steps, batch mode, the learned
-preconditioner, the next rows) are printed on lines of their own before the final line.
+preconditioner, the next rows, the pf+g9/2 12p+12n workload at 2M_z = 0 and 4) are printed
+on lines of their own before the final line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -390,8 +391,9 @@ def run_pfg(P, M_max):
     2048(1) capped at M_max.  Per sweep: seconds (CUDA events), H_eff TFLOP/s on the device,
     energy.  The learned preconditioner is trained on the 2M_z = 0 instance (samples
     harvested during its M = 1024 sweeps) and evaluated on the held-out 2M_z = 4 instance:
-    Davidson from the uniform guess at the middle positions of its final block state, with
-    the diagonal and with the learned preconditioner."""
+    along a left-to-right half sweep at its final M, Davidson from the uniform guess at every
+    fourth position with the diagonal and with the learned preconditioner (products,
+    convergence, energies)."""
     import numpy as np
     import torch
     from gen import make_problem, initial_mps
@@ -440,24 +442,30 @@ def run_pfg(P, M_max):
             # fourth position with each preconditioner, then the step itself
             d.mlp_set_params(theta)
             M = sweeps[-1]["M"]
-            n_diag = n_mlp = 0
-            dmax = 0.0
+            ev = {"diagonal": [], "learned": []}
             for p in range(1, N - 2):
                 if p % 4 == 0:
                     size = d.psi_layout(p)["size"]
                     x0 = torch.ones(size, dtype=torch.float64, device="cuda")
+                    for name, pc in (("diagonal", P.PRECOND_DIAG), ("learned", P.PRECOND_MLP)):
+                        d.set_options(precision=P.MIXED_FP32, precond=pc)
+                        e, st = d.davidson(p, guess=x0, allow_noconv=True)
+                        ev[name].append((e, st["n_products"], st["converged"]))
                     d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
-                    ea, sa = d.davidson(p, guess=x0, allow_noconv=True)
-                    d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_MLP)
-                    eb, sb = d.davidson(p, guess=x0, allow_noconv=True)
-                    d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
-                    n_diag += sa["n_products"]
-                    n_mlp += sb["n_products"]
-                    dmax = max(dmax, abs(ea - eb))
                 d.step(p, 0, M)
-            res["precond_held_out"] = {"positions": "every fourth of 1..%d at M=%d" % (N - 3, M),
-                                       "products_diagonal": n_diag, "products_learned": n_mlp,
-                                       "max_dE": dmax}
+            both = [abs(a[0] - b[0]) for a, b in zip(ev["diagonal"], ev["learned"])
+                    if a[2] and b[2]]
+            res["precond_held_out"] = {
+                "positions": "every fourth of 1..%d at M=%d, Davidson from the uniform guess "
+                             "(at most 100 products)" % (N - 3, M),
+                "evaluated": len(ev["diagonal"]),
+                "products_diagonal": sum(x[1] for x in ev["diagonal"]),
+                "products_learned": sum(x[1] for x in ev["learned"]),
+                "converged_diagonal": sum(x[2] for x in ev["diagonal"]),
+                "converged_learned": sum(x[2] for x in ev["learned"]),
+                "max_dE_both_converged": max(both) if both else None,
+                "energies_diagonal": [x[0] for x in ev["diagonal"]],
+                "energies_learned": [x[0] for x in ev["learned"]]}
         d.close()
         out["two_Mz_%d" % tmz] = res
     return out
