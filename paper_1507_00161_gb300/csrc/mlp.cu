@@ -4,9 +4,12 @@
 //
 // Parameters (packed, row-major): W1 (256 x 4), b1, W2 (256 x 256), b2, W3 (256 x 256),
 // b3, w4 (256), b4 (1).  Activations are row-major (rows = samples).  The dense layers
-// run on the library's tiled GEMM (task lists), everything else in the kernels below.
+// run on the library's grouped GEMM: the FP32 network on the split-TF32 tensor-core engine
+// (FP32 accuracy), the FP64 one (gradient checks) on the FP64 tiles; everything else in the
+// kernels below.
 // Loss: mean squared error; optimizer: Adam.
 #include <cmath>
+#include <type_traits>
 
 #include "common.h"
 
@@ -216,12 +219,21 @@ static void gemm(T* C, int ldc, const T* A, int lda, bool ta, const T* B, int ld
   be[B_U] = nB;
   be[B_Y] = nC;
   DevTaskList d;
-  d.build(L, be, s);
-  Bases<T> b{};
-  b.p[B_X] = const_cast<T*>(A);
-  b.p[B_U] = const_cast<T*>(B);
-  b.p[B_Y] = C;
-  run_gemm_tasks<T>(d, b, 1, s);
+  if constexpr (std::is_same<T, float>::value) {
+    d.build(L, be, s, 0);   // every task in 64 x 64 tensor-core tiles
+    Bases<void> b{};
+    b.p[B_X] = const_cast<T*>(A);
+    b.p[B_U] = const_cast<T*>(B);
+    b.p[B_Y] = C;
+    run_gemm_tasks_tc<float, float, float>(d, b, 1, s);
+  } else {
+    d.build(L, be, s);
+    Bases<T> b{};
+    b.p[B_X] = const_cast<T*>(A);
+    b.p[B_U] = const_cast<T*>(B);
+    b.p[B_Y] = C;
+    run_gemm_tasks<T>(d, b, 1, s);
+  }
   DMRG_CUDA(cudaStreamSynchronize(s));   // the list buffers are released on return
 }
 
