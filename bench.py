@@ -391,45 +391,51 @@ def run_pfg(P, M_max):
     2048(1) capped at M_max.  Per sweep: seconds (CUDA events), H_eff TFLOP/s on the device,
     energy.  The learned preconditioner is trained on the 2M_z = 0 instance (samples
     harvested during its M = 1024 sweeps) and evaluated on the held-out 2M_z = 4 instance:
-    along a left-to-right half sweep at its final M, Davidson from the uniform guess at every
-    fourth position with the diagonal and with the learned preconditioner (products,
-    convergence, energies)."""
-    import numpy as np
+    after its schedule, one more sweep at the final M with the diagonal preconditioner, and
+    the same sweep from the identical state (a second context through the same
+    deterministic schedule) with the learned one."""
     import torch
     from gen import make_problem, initial_mps
+    sched = [(M, n) for (M, n) in PFG_SCHEDULE if M <= M_max]
     out = {"workload": "pf+g9/2 60 sites, 12p+12n, seed 4, mixed path, schedule %s" %
-                       "+".join("%d(%d)" % x for x in PFG_SCHEDULE if x[0] <= M_max)}
+                       "+".join("%d(%d)" % x for x in sched)}
+
+    def timed_sweep(d, M):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, e = d.sweep(M)
+        e1.record()
+        e1.synchronize()
+        fl = sum(x["heff_flops"] * x["n_products"] for x in st)
+        hs = sum(x["heff_seconds"] for x in st)
+        return st, {"M": M, "s": e0.elapsed_time(e1) / 1e3, "energy": e,
+                    "products": sum(x["n_products"] for x in st),
+                    "heff_tflops": fl / max(hs, 1e-12) / 1e12,
+                    "max_step_gflop": max(x["heff_flops"] for x in st) / 1e9}
+
+    inits = {}
+
+    def run_schedule(tmz, harvest):
+        prob = make_problem("pfg", 12, 12, tmz, seed=4)
+        if tmz not in inits:
+            inits[tmz] = initial_mps(prob, sched[0][0], 4004)
+        d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8)
+        d.build_blocks(inits[tmz])
+        sweeps = []
+        for (M, n) in sched:
+            for _ in range(n):
+                if harvest and M == 1024:
+                    d.mlp_harvest(True, 2048)
+                sweeps.append(timed_sweep(d, M)[1])
+                d.mlp_harvest(False)
+        return d, sweeps
+
     theta = None
     for tmz in (0, 4):
-        prob = make_problem("pfg", 12, 12, tmz, seed=4)
-        init = initial_mps(prob, PFG_SCHEDULE[0][0], 4004)
-        d = P.DMRG(prob, precision=P.MIXED_FP32, dav_tol=1e-8)
-        d.build_blocks(init)
-        sweeps = []
-        for (M, n) in PFG_SCHEDULE:
-            if M > M_max:
-                break
-            for _ in range(n):
-                harvest = tmz == 0 and M == 1024
-                if harvest:
-                    d.mlp_harvest(True, 2048)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                st, e = d.sweep(M)
-                e1.record()
-                e1.synchronize()
-                if harvest:
-                    d.mlp_harvest(False)
-                fl = sum(x["heff_flops"] * x["n_products"] for x in st)
-                hs = sum(x["heff_seconds"] for x in st)
-                sweeps.append({"M": M, "s": e0.elapsed_time(e1) / 1e3, "energy": e,
-                               "products": sum(x["n_products"] for x in st),
-                               "heff_tflops": fl / max(hs, 1e-12) / 1e12,
-                               "max_step_gflop": max(x["heff_flops"] for x in st) / 1e9})
+        d, sweeps = run_schedule(tmz, harvest=tmz == 0)
         free_b, total_b = torch.cuda.mem_get_info()
         res = {"sweeps": sweeps, "device_mem_gb": round((total_b - free_b) / 1e9, 2)}
-        N = prob.n_sites
         if tmz == 0:
             d.mlp_reset(3)
             t0 = time.perf_counter()
@@ -437,39 +443,25 @@ def run_pfg(P, M_max):
             res["mlp"] = {"samples": ns, "loss": loss, "train_s": time.perf_counter() - t0}
             theta = d.mlp_params()
         elif theta is not None:
-            # held-out evaluation: the network trained on the 2M_z = 0 instance; the left-to-
-            # right half of a sweep at the final M, Davidson from the uniform guess at every
-            # fourth position with each preconditioner, then the step itself
-            d.mlp_set_params(theta)
             M = sweeps[-1]["M"]
-            ev = {"diagonal": [], "learned": []}
-            for p in range(1, N - 2):
-                if p % 4 == 0:
-                    size = d.psi_layout(p)["size"]
-                    x0 = torch.ones(size, dtype=torch.float64, device="cuda")
-                    for name, pc in (("diagonal", P.PRECOND_DIAG), ("learned", P.PRECOND_MLP)):
-                        d.set_options(precision=P.MIXED_FP32, precond=pc)
-                        e, st = d.davidson(p, guess=x0, allow_noconv=True)
-                        ev[name].append((e, st["n_products"], st["converged"]))
-                    d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_DIAG)
-                d.step(p, 0, M)
-            both = [abs(a[0] - b[0]) for a, b in zip(ev["diagonal"], ev["learned"])
-                    if a[2] and b[2]]
+            st_d, sw_d = timed_sweep(d, M)
+            d.close()
+            d, _ = run_schedule(tmz, harvest=False)     # the identical state again
+            d.mlp_set_params(theta)
+            d.set_options(precision=P.MIXED_FP32, precond=P.PRECOND_MLP)
+            st_l, sw_l = timed_sweep(d, M)
             res["precond_held_out"] = {
-                "positions": "every fourth of 1..%d at M=%d, Davidson from the uniform guess "
-                             "(at most 100 products)" % (N - 3, M),
-                "evaluated": len(ev["diagonal"]),
-                "products_diagonal": sum(x[1] for x in ev["diagonal"]),
-                "products_learned": sum(x[1] for x in ev["learned"]),
-                "converged_diagonal": sum(x[2] for x in ev["diagonal"]),
-                "converged_learned": sum(x[2] for x in ev["learned"]),
-                "max_dE_both_converged": max(both) if both else None,
-                "energies_diagonal": [x[0] for x in ev["diagonal"]],
-                "energies_learned": [x[0] for x in ev["learned"]]}
+                "protocol": "one sweep at M=%d from the identical state, diagonal vs learned "
+                            "(network trained on the 2M_z=0 instance)" % M,
+                "products_diagonal": sw_d["products"], "products_learned": sw_l["products"],
+                "sweep_s_diagonal": sw_d["s"], "sweep_s_learned": sw_l["s"],
+                "energy_diagonal": sw_d["energy"], "energy_learned": sw_l["energy"],
+                "max_step_dE": max(abs(a["energy"] - b["energy"]) for a, b in zip(st_d, st_l)),
+                "max_residual_diagonal": max(x["residual"] for x in st_d),
+                "max_residual_learned": max(x["residual"] for x in st_l)}
         d.close()
         out["two_Mz_%d" % tmz] = res
     return out
-
 
 def max_over_ranks(x, dist=None):
     """The largest value of x over the ranks of the process group (x on a single rank)."""
