@@ -397,9 +397,9 @@ int dmrg_get_tuning(dmrg_ctx* ctx, dmrg_tuning* t);
 /* Autotuner of the product's work split (dmrg_tuning.heff_big_edge), on the superblock at
  * position p (not in the paper): one H_eff product is timed for each candidate edge (0 =
  * fused tile kernels only, then 32, 64, 128, 256) with CUDA events on the context stream,
- * best of reps >= 1 after two untimed products (the second captures the graph); the fastest is kept, and within 5 % of it
- * the smallest positive edge (its grouped passes sum their products with compensation and
- * are the more accurate).  The edge is set as by dmrg_set_tuning; the products agree to
+ * best of reps >= 1 after two untimed products (the second captures the graph); the
+ * fastest is kept, and within 5 % of it the smallest positive edge (its grouped passes sum
+ * their products with compensation and are the more accurate).  The edge is set as by dmrg_set_tuning; the products agree to
  * rounding whichever is chosen, but the choice follows measured times.  chosen: the edge
  * set; edges, ms (optional host arrays of 5): the candidates and their best times.  Call
  * between steps (the superblock held by the context is dropped).  DMRG_EINVAL for a
