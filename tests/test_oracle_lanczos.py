@@ -29,7 +29,8 @@ def test_product_equals_dense_matrix(space, Np, Nn, tM, seed):
 
 
 @pytest.mark.parametrize("space,Np,Nn,tM,seed", [("sd", 2, 2, 0, 1), ("sd", 3, 2, 1, 4),
-                                                  ("p", 2, 2, 0, 8), ("sd", 2, 2, 4, 1)])
+                                                  ("p", 2, 2, 0, 8), ("sd", 2, 2, 4, 1),
+                                                  ("pfg", 1, 1, 4, 5)])
 def test_lowest_equals_dense_eigh(space, Np, Nn, tM, seed):
     p = make_problem(space, Np, Nn, tM, seed=seed)
     r = lanczos_lowest(p, Np, Nn, tM, tol=1e-10, threads=2, want_vector=True)
@@ -87,3 +88,23 @@ def test_rejects_non_hermitian_list():
     q = dataclasses.replace(p, v_val=vv)
     with pytest.raises(ValueError):
         lanczos_lowest(q)
+
+
+def test_stored_pfg_sweep_is_variational():
+    """The stored oracle sweep on the pf+g9/2 space (tests/golden/pfg_2p2n_M4.json: 2p+2n,
+    2M_z = 4, M = 16) lies above the exact energy of that sector (Lanczos, dimension 15,372)
+    at every step, and the exact 2M_z = 4 energy lies above the 2M_z = 0 one (rotational
+    invariance: the M_z = 2 states are the J >= 2 states of the M_z = 0 spectrum)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pfg_2p2n_M4.json")
+    with open(path) as f:
+        g = json.load(f)
+    p4 = make_problem("pfg", 2, 2, 4, seed=5)
+    r4 = lanczos_lowest(p4, tol=1e-10, threads=2)
+    assert r4["dim"] == 15372 == mscheme_dimension("pfg", 2, 2, 4)
+    assert r4["residual"] <= 1e-9
+    for st in g["steps"]:
+        assert st["energy"] >= r4["energy"] - 1e-9, (st["p"], st["dir"])
+    r0 = lanczos_lowest(make_problem("pfg", 2, 2, 0, seed=5), tol=1e-10, threads=2)
+    assert r4["energy"] >= r0["energy"] - 1e-9
