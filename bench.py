@@ -608,50 +608,51 @@ def run_gpu(args):
     # the FP64 eigenvector (its Davidson then needs one product: the sweep time is, if
     # anything, slightly in FP64's favour)
     fp64 = {}
-    try:
-        finish = [(p, 0) for p in range(timed[-1][0] + 1, N - 2)] + \
-                 [(p, 1) for p in range(N - 3, 0, -1)]
-        for (p, dr) in finish:          # complete the mixed sweep the timed steps are in
-            d.step(p, dr, M)
-        seq = [(p, 0) for p in range(1, N - 2)] + [(p, 1) for p in range(N - 3, 0, -1)]
-        q = N // 2
-        fs = []
-        for _ in range(max(args.fp64_sweeps, 1) if args.fp64_sweeps > 0 else 0):
-            d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
-            ms, products, e = 0.0, 0, None
-            for (p, dr) in seq:
-                if p == q and dr == 0 and not fp64:
-                    d.set_options(precision=P.MIXED_FP32, dav_tol=1e-8,
-                                  dav_max_iter=args.max_iter)
-                    size = d.psi_layout(q)["size"]
-                    psi_m = torch.empty(size, dtype=torch.float64, device="cuda")
-                    e_mixed, st_m = d.davidson(q, out=psi_m, allow_noconv=True)
-                    d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
-                    c2 = d.counters()
-                    e_fp64, st_d = d.davidson(q, guess=psi_m, allow_noconv=True)
-                    c3 = d.counters()
-                    fp64 = {"position": q, "energy": e_fp64, "energy_mixed": e_mixed,
-                            "dE_mixed_vs_fp64": abs(e_mixed - e_fp64),
-                            "products_mixed": st_m["n_products"],
-                            "products_fp64_from_mixed_vector": st_d["n_products"],
-                            "converged": [st_m["converged"], st_d["converged"]],
-                            "heff_tflops": (c3["heff_flops"] - c2["heff_flops"])
-                            / max(c3["heff_seconds"] - c2["heff_seconds"], 1e-12) / 1e12}
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                st = d.step(p, dr, M)
-                e1.record()
-                e1.synchronize()
-                ms += e0.elapsed_time(e1)
-                products += st["n_products"]
-                e = st["energy"]
-            fs.append({"s": ms / 1e3, "energy": e, "products": products})
-        if fs:
-            fp64["sweep_s"] = statistics.median(x["s"] for x in fs)
-            fp64["sweeps"] = fs
-    except Exception as exc:        # a side measurement never takes the bench line down
-        fp64 = {"error": str(exc)}
+    if rank == 0:    # side measurements: rank 0 only (replicas repeat the same work)
+        try:
+            finish = [(p, 0) for p in range(timed[-1][0] + 1, N - 2)] + \
+                     [(p, 1) for p in range(N - 3, 0, -1)]
+            for (p, dr) in finish:          # complete the mixed sweep the timed steps are in
+                d.step(p, dr, M)
+            seq = [(p, 0) for p in range(1, N - 2)] + [(p, 1) for p in range(N - 3, 0, -1)]
+            q = N // 2
+            fs = []
+            for _ in range(max(args.fp64_sweeps, 1) if args.fp64_sweeps > 0 else 0):
+                d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
+                ms, products, e = 0.0, 0, None
+                for (p, dr) in seq:
+                    if p == q and dr == 0 and not fp64:
+                        d.set_options(precision=P.MIXED_FP32, dav_tol=1e-8,
+                                      dav_max_iter=args.max_iter)
+                        size = d.psi_layout(q)["size"]
+                        psi_m = torch.empty(size, dtype=torch.float64, device="cuda")
+                        e_mixed, st_m = d.davidson(q, out=psi_m, allow_noconv=True)
+                        d.set_options(precision=P.FP64, dav_tol=1e-8, dav_max_iter=args.max_iter)
+                        c2 = d.counters()
+                        e_fp64, st_d = d.davidson(q, guess=psi_m, allow_noconv=True)
+                        c3 = d.counters()
+                        fp64 = {"position": q, "energy": e_fp64, "energy_mixed": e_mixed,
+                                "dE_mixed_vs_fp64": abs(e_mixed - e_fp64),
+                                "products_mixed": st_m["n_products"],
+                                "products_fp64_from_mixed_vector": st_d["n_products"],
+                                "converged": [st_m["converged"], st_d["converged"]],
+                                "heff_tflops": (c3["heff_flops"] - c2["heff_flops"])
+                                / max(c3["heff_seconds"] - c2["heff_seconds"], 1e-12) / 1e12}
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    st = d.step(p, dr, M)
+                    e1.record()
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    products += st["n_products"]
+                    e = st["energy"]
+                fs.append({"s": ms / 1e3, "energy": e, "products": products})
+            if fs:
+                fp64["sweep_s"] = statistics.median(x["s"] for x in fs)
+                fp64["sweeps"] = fs
+        except Exception as exc:        # a side measurement never takes the bench line down
+            fp64 = {"error": str(exc)}
     d.close()
     del d
     at_M = [x["s"] for x in sweeps if x["M"] == M]
@@ -671,23 +672,18 @@ def run_gpu(args):
                                                            "sb_terms", "sb_tiles",
                                                            "sb_small_tiles", "sb_term_hist")}})
         _emit("fp64", fp64)
-    batch = run_batch_compare(P, args.batch_mcap) if args.batch_mcap > 0 else None
-    if rank == 0 and batch:
-        _emit("batch", batch)
-    precond = run_precond_compare(P) if args.precond else None
-    if rank == 0 and precond:
-        _emit("precond", precond)
-    if args.next_rows:
-        nr = run_next_rows(P, prob, init, M, None)
-        if rank == 0:
-            _emit("next_rows", nr)
-    if args.pfg_mmax > 0:
+    if rank == 0 and args.batch_mcap > 0:
+        _emit("batch", run_batch_compare(P, args.batch_mcap))
+    if rank == 0 and args.precond:
+        _emit("precond", run_precond_compare(P))
+    if rank == 0 and args.next_rows:
+        _emit("next_rows", run_next_rows(P, prob, init, M, None))
+    if rank == 0 and args.pfg_mmax > 0:
         try:
             pfg = run_pfg(P, args.pfg_mmax)
         except Exception as exc:      # a side measurement never takes the bench line down
             pfg = {"error": str(exc)}
-        if rank == 0:
-            _emit("pfg", pfg)
+        _emit("pfg", pfg)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
