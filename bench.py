@@ -166,7 +166,7 @@ def cpu_oracle_sample(steps, warmup, budget_s=20.0, M0=None):
     for _ in range(max(1, warmup)):
         sb.apply(x)
     n, t = 0, 0.0
-    while n < max(1, steps) or t < min(budget_s, 2.0):
+    while n < max(1, steps) or t < min(budget_s, 10.0):
         t0 = time.perf_counter()
         sb.apply(x)
         t += time.perf_counter() - t0
