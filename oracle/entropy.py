@@ -91,14 +91,16 @@ def entropies(rho):
 # ----------------------------------------------------------------------------------
 # every orbital pair, from the state written out in the occupation basis
 # ----------------------------------------------------------------------------------
-def _block_patterns(o):
+def _block_patterns(o, p=None):
     """Left blocks (bonds 0..N-3) and right blocks (bonds 2..N-2) of an OracleDMRG as
-    {sector: (occupation bitmasks over chain positions, coefficients patterns x m)}."""
+    {sector: (occupation bitmasks over chain positions, coefficients patterns x m)}; with p
+    given, only the blocks the superblock at p is built from (left bonds < p, right bonds
+    > p), which are consistent with each other in the middle of a sweep."""
     from .dmrg import enlarge_left, enlarge_right, vacuum
     N = o.N
     left, right = {}, {}
     prev = {(0, 0, 0): ([0], np.ones((1, 1)))}
-    for b in range(0, N - 2):
+    for b in range(0, N - 2 if p is None else p):
         if b not in o.UL:
             break
         blk = vacuum(1, 0) if b == 0 else o.left[b - 1]
@@ -109,7 +111,7 @@ def _block_patterns(o):
             cur[Q] = (pats, E @ U)
         left[b] = prev = cur
     prev = {(0, 0, 0): ([0], np.ones((1, 1)))}
-    for b in range(N - 2, 1, -1):
+    for b in range(N - 2, 1 if p is None else p, -1):
         if b not in o.UR:
             break
         blk = vacuum(1, 0) if b == N - 2 else o.right[b + 1]
@@ -141,7 +143,7 @@ def state_amplitudes(o):
     """The wave function of the last step of an OracleDMRG written out: {occupation
     bitmask over chain positions: amplitude} (tensor basis in chain order)."""
     p = o.psi_at[0]
-    left, right = _block_patterns(o)
+    left, right = _block_patterns(o, p)
     lb, rb = left[p - 1], right[p + 1]
     Lenl, Renl = o._prev_L, o._prev_R
     amp = {}
