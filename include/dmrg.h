@@ -256,6 +256,23 @@ int dmrg_rdm_eigh(dmrg_ctx* ctx, int32_t p, int32_t dir, int32_t cluster, int32_
  * neighbouring pair.  DMRG_EINVAL if no wave function is held for p. */
 int dmrg_dot_rdm(dmrg_ctx* ctx, int32_t p, double* rho, double* ent);
 
+/* All-pairs orbital mutual information I_ij and one-orbital entropies s_i of the paper's
+ * entanglement analysis (the quantities its orbital ordering is computed from), on the
+ * device, from one left-to-right half sweep at M (positions 1..N-3, each as dmrg_step with
+ * dir 0; the blocks and the held state change as in that half sweep).  The occupation and
+ * the creation operator of every orbital of the growing left block are carried through the
+ * renormalizations; the pair (i, j), i < j, is evaluated from the wave function of the
+ * step where j is the left dot (j <= N-3), and the pairs with the last two chain positions
+ * at the last step.  Each pair's two-orbital density matrix (basis |n_i n_j>, off-diagonal
+ * <c+_i c_j>, nonzero only for equal species and m) gives s_i, s_j, s_ij and
+ * I_ij = s_i + s_j - s_ij >= 0 (natural logarithms; the paper prints the opposite sign).
+ * I: host array N x N, row-major, indexed by the problem's sites (not chain positions),
+ * zero diagonal; s: host array N, from the last step's wave function; steps: optional host
+ * array of N-3 step records.  DMRG_EINVAL before dmrg_build_blocks, for M < 1, NULL outputs
+ * or two targeted states; DMRG_ENOCONV as dmrg_step (the results are still written). */
+int dmrg_mutual_information(dmrg_ctx* ctx, int32_t M, double* I, double* s,
+                            dmrg_step_stats* steps);
+
 /* Dynamic block state selection (DBSS): the number of kept block states is set by the
  * truncation error instead of being fixed ("M_max determined by the truncation error
  * delta eps_TR" of the method section; the paper's runs use M_min = 256 and delta eps_TR =

@@ -28,6 +28,7 @@ EXPORTED = ["dmrg_create", "dmrg_destroy", "dmrg_last_error", "dmrg_build_blocks
             "dmrg_rdm_eigh", "dmrg_set_tuning", "dmrg_get_tuning", "dmrg_partition_terms",
             "dmrg_autotune",
             "dmrg_set_options", "dmrg_set_dbss", "dmrg_set_roots", "dmrg_dot_rdm",
+            "dmrg_mutual_information",
             "dmrg_get_counters",
             "dmrg_heff_cost",
             "dmrg_heff_apply_noalloc", "dmrg_mlp_reset", "dmrg_mlp_harvest", "dmrg_mlp_train",
@@ -140,6 +141,7 @@ def load_library(path: str = LIB_PATH):
         "dmrg_set_dbss": [P, i32, dbl],
         "dmrg_set_roots": [P, i32],
         "dmrg_dot_rdm": [P, i32, P, P],
+        "dmrg_mutual_information": [P, i32, P, P, P],
         "dmrg_rdm_eigh": [P, i32, i32, i32, P, P, P, P, P, P],
         "dmrg_set_tuning": [P, ctypes.POINTER(Tuning)],
         "dmrg_partition_terms": [P, i32, P],
@@ -282,6 +284,16 @@ class DMRG:
         ent = np.zeros(4)
         self._check(self.lib.dmrg_dot_rdm(self.h, int(p), _np_ptr(rho), _np_ptr(ent)))
         return rho.reshape(4, 4), tuple(float(x) for x in ent)
+
+    def mutual_information(self, M):
+        """All-pairs orbital mutual information from a left-to-right half sweep at M
+        (dmrg_mutual_information): (I (N x N, problem sites), s (N), step records)."""
+        N = self.n_sites
+        I = np.zeros(N * N)
+        s = np.zeros(N)
+        arr = (StepStats * (N - 3))()
+        self._check(self.lib.dmrg_mutual_information(self.h, int(M), _np_ptr(I), _np_ptr(s), arr))
+        return I.reshape(N, N), s, [a.as_dict() for a in arr]
 
     def partition_terms(self, b):
         """Number of operator products across bond b of the operator partition."""

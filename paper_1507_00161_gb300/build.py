@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libdmrg.so")
-SOURCES = ["problem.cu", "kernels.cu", "heff.cu", "heff_tc.cu", "heff_small.cu", "mlp.cu", "renorm.cu", "svd.cu", "tgemm.cu", "dmrg.cu", "noalloc.cu", "extrapolate.cu", "entropy.cu", "ordering.cu"]
+SOURCES = ["problem.cu", "kernels.cu", "heff.cu", "heff_tc.cu", "heff_small.cu", "mlp.cu", "renorm.cu", "svd.cu", "tgemm.cu", "dmrg.cu", "noalloc.cu", "extrapolate.cu", "entropy.cu", "ordering.cu", "mutual.cu"]
 HEADERS = ["common.h", "problem.h"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
          "-Xcompiler", "-fPIC"]

@@ -397,6 +397,26 @@ struct RdmTask {
 // the five sums of the dot density matrix; d_part holds one double per task
 void rdm_sums(const RdmTask* d_tasks, int64_t n, const double* psi, double* d_part,
               double* d_out, cudaStream_t s);
+
+// all-pairs mutual information (mutual.cu): rectangle dot products (lda < 0: trace of the
+// B rectangle), their sums per slot (slots = consecutive task ranges), and the embedding of
+// operator blocks (src < 0: an identity) into the blocks of an enlarged operator
+struct RectDot {
+  int64_t a, b;
+  int32_t lda, ldb, nr, nc;
+  double sign;
+};
+struct EmbedTask {
+  int64_t src, dst;
+  int32_t lds, ldd, nr, nc;
+  double sign;
+};
+void rect_dots(const RectDot* d_tasks, int64_t n, const double* A, const double* B,
+               double* d_part, cudaStream_t s);
+void slot_sums(const int64_t* d_ptr, int64_t n_slots, const double* d_part, double* d_out,
+               cudaStream_t s);
+void embed_blocks(const EmbedTask* d_tasks, int64_t n, const double* S, double* D,
+                  cudaStream_t s);
 // global selection: k-th largest of w[0..n) (ties irrelevant for the value) in out[0] and k
 // in out[1]; k = kmax, or with target > 0 the smallest k in [kmin, kmax] whose discarded
 // weight 1 - (sum of the k largest) is at most target (kmax if none)

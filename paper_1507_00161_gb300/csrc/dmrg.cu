@@ -263,6 +263,7 @@ struct dmrg_ctx {
   // precomputed per-site W entry orders (grouped by destination label)
   std::vector<std::vector<int>> w_by_b, w_by_a;
   std::vector<dmrg::SiteEntries> ent_left, ent_right;
+  std::vector<int32_t> order;   // chain position -> site of the problem
   // learned preconditioner: parameters, Adam moments, harvested samples, Davidson history
   dmrg::DevBuf<float> mlp_p, mlp_g, mlp_m, mlp_v, mlp_samples, mlp_X, mlp_T, mlp_feat;
   dmrg::MlpActs<float> mlp_acts;
@@ -2483,8 +2484,455 @@ static double now_s() {
 
 // late_energy: in a sweep, the mixed path's energy of this step is stored there once the next
 // step has built its superblock (its Rayleigh quotient overlaps that host work)
+// ---------------------------------------------------------------------------------------
+// all-pairs orbital mutual information along a left-to-right half sweep.  The occupation
+// n_i and the creation operator c+_i of every orbital i of the left block are carried
+// through the renormalizations (label 2i: n_i, 2i+1: c+_i with the Jordan-Wigner string of
+// the block's earlier orbitals).  At step p the pairs (i, p), i < p, are read off the
+// wave function's density matrix on the enlarged left block, rho = psi psi^T per block:
+//   <n_i> = sum_sigma n_i . rho[sigma sigma],  <n_i n_p> = n_i . rho[1 1],
+//   <c+_i c_p> = (-1)^{N(q)} c+_i . rho[0 1]   (same species and 2m only; q: the block
+//   sector of the occupied piece),
+// and at the last step (p = N-3) the pairs with the right dot N-2 and with the right
+// block's single orbital N-1 from the wave function's columns, whose occupations are
+// explicit there: column-restricted density matrices for the diagonal terms, transition
+// matrices between blocks for the hops.  Each pair's two-orbital density matrix (basis
+// |n_i n_j>, off-diagonal <c+_i c_j>) then gives s_i, s_j, s_ij and I_ij = s_i + s_j - s_ij.
+// ---------------------------------------------------------------------------------------
+struct MiRun {
+  OpSet ops;                    // carried operators on the left block of the current step
+  int N = 0;
+  std::vector<double> I, s;     // chain positions
+};
+
+static bool mi_piece(const Layout& L, int Q, int sg, int* off, int* len) {
+  if (L.pblk[Q][sg] < 0) return false;
+  const int D = L.sec.d[Q];
+  *off = L.poff[Q][sg];
+  *len = (sg == 0 && L.pblk[Q][1] >= 0 ? L.poff[Q][1] : D) - *off;
+  return *len > 0;
+}
+
+static double mi_vn(std::initializer_list<double> w) {
+  double s = 0.0;
+  for (double x : w)
+    if (x > 0.0) s -= x * std::log(x);
+  return s;
+}
+
+// s_i, s_j and I_ij of two orbitals from <n_i>, <n_j>, <n_i n_j> and <c+_i c_j>
+static void mi_pair(double ni, double nj, double nij, double h, double* si, double* sj,
+                    double* I) {
+  const double p11 = nij, p10 = ni - nij, p01 = nj - nij, p00 = 1.0 - ni - nj + nij;
+  const double mid = 0.5 * (p01 + p10);
+  const double rad = std::sqrt(0.25 * (p01 - p10) * (p01 - p10) + h * h);
+  *si = mi_vn({1.0 - ni, ni});
+  *sj = mi_vn({1.0 - nj, nj});
+  *I = *si + *sj - mi_vn({p00, p11, mid + rad, mid - rad});
+}
+
+// the left block of bond 0 (orbital 0 alone): n_0 and c+_0 on its sectors of one state
+static void mi_init(Ctx& c, MiRun& mr) {
+  const OpSet& L0 = c.left[0].ops;
+  DMRG_REQUIRE(c.left[0].valid, DMRG_EINVAL, "blocks are not built");
+  OpSet& o = mr.ops;
+  o = OpSet();
+  o.sec = L0.sec;
+  o.nlab = 2;
+  o.lab_ptr.assign(3, 0);
+  const QN q0 = c.chain.q[0], vac{0, 0, 0};
+  std::vector<double> h;
+  for (int s = 0; s < o.sec.size(); ++s) {
+    DMRG_REQUIRE(o.sec.d[s] == 1, DMRG_EINVAL, "internal: the block of bond 0 is not one orbital");
+    o.blocks.push_back(OpBlock{s, s, int64_t(h.size())});
+    h.push_back(o.sec.q[s] == q0 ? 1.0 : 0.0);
+  }
+  o.lab_ptr[1] = int64_t(o.blocks.size());
+  const int se = o.sec.find(vac), so = o.sec.find(q0);
+  if (se >= 0 && so >= 0) {
+    o.blocks.push_back(OpBlock{so, se, int64_t(h.size())});
+    h.push_back(1.0);
+  }
+  o.lab_ptr[2] = int64_t(o.blocks.size());
+  o.n_elems = int64_t(h.size());
+  o.data.upload(h, c.stream);
+  o.index_by_in();
+}
+
+// rectangle checks against the buffers they read
+static void mi_check(const RectDot& t, int64_t nA, int64_t nB) {
+  DMRG_REQUIRE(t.nr >= 0 && t.nc >= 0 && t.b >= 0 && t.nc <= t.ldb, DMRG_EINVAL,
+               "internal: density rectangle malformed");
+  if (t.nr == 0 || t.nc == 0) return;
+  DMRG_REQUIRE(t.b + int64_t(t.nr - 1) * t.ldb + t.nc <= nB, DMRG_EINVAL,
+               "internal: density rectangle outside its matrix");
+  if (t.lda < 0) {
+    DMRG_REQUIRE(t.nr == t.nc, DMRG_EINVAL, "internal: trace of a non-square rectangle");
+  } else {
+    DMRG_REQUIRE(t.a >= 0 && t.nc <= t.lda && t.a + int64_t(t.nr - 1) * t.lda + t.nc <= nA,
+                 DMRG_EINVAL, "internal: operator rectangle outside the carried operators");
+  }
+}
+
+static void mi_measure(Ctx& c, MiRun& mr, Super& sb, int p) {
+  const int N = c.N;
+  const bool last = p == N - 3;
+  const Layout& Ll = sb.Ll;
+  const Layout& Rl = sb.Rl;
+  const OpSet& B = mr.ops;
+  const int nsB = B.sec.size();
+  DMRG_REQUIRE(c.left[p - 1].ops.sec.q == B.sec.q && c.left[p - 1].ops.sec.d == B.sec.d,
+               DMRG_EINVAL, "internal: carried operators do not match the left block");
+  const int nb = int(sb.bL.size());
+  const QN vac{0, 0, 0};
+  const QN qp = c.chain.q[p];
+  auto parity = [](const QN& q) { return ((q.a + q.b) & 1) ? -1.0 : 1.0; };
+  // ---- density and transition matrices of the wave function (FP64 GEMM tasks)
+  TaskList T;
+  int64_t roff = 0;
+  auto matrix = [&](int rows, int cols) {
+    const int64_t o = roff;
+    T.begin_task(Operand{o, B_Y, cols}, rows, cols);
+    roff += int64_t(rows) * cols;
+    return o;
+  };
+  std::vector<int64_t> rho(nb);
+  for (int b = 0; b < nb; ++b) {
+    const int D = sb.bdl[b], dR = sb.bdr[b];
+    rho[b] = matrix(D, D);
+    T.add_term(Operand{sb.boff[b], B_X, dR}, Operand{sb.boff[b], B_X, dR}, dR, 2, 1.0);
+  }
+  // last step: columns of every block with the occupations of N-2 (right dot) and N-1
+  struct Col {
+    int off, sg, occ;
+  };
+  std::vector<std::vector<Col>> cols(nb);
+  std::vector<int64_t> s_rd(nb, -1), s_rs(nb, -1), s_rr(nb, -1), t_rr(nb, -1);
+  std::vector<int64_t> t_j[2] = {std::vector<int64_t>(nb, -1), std::vector<int64_t>(nb, -1)};
+  std::vector<int> b2_j[2] = {std::vector<int>(nb, -1), std::vector<int>(nb, -1)};
+  const QN q_rd = last ? c.chain.q[N - 2] : vac, q_rs = last ? c.chain.q[N - 1] : vac;
+  if (last) {
+    for (int b = 0; b < nb; ++b) {
+      const int jR = sb.bR[b];
+      const QN QR = Rl.sec.q[jR];
+      for (int sg = 0; sg < 2; ++sg) {
+        int off, len;
+        if (!mi_piece(Rl, jR, sg, &off, &len)) continue;
+        const QN r = sg ? QR - q_rd : QR;
+        DMRG_REQUIRE(len == 1 && (r == vac || r == q_rs), DMRG_EINVAL,
+                     "internal: the last right block is not one orbital");
+        cols[b].push_back(Col{off, sg, r == q_rs ? 1 : 0});
+      }
+    }
+    auto select = [&](int b, int want_rd, int want_rs) -> int64_t {
+      std::vector<int> pick;
+      for (const Col& k : cols[b])
+        if ((want_rd < 0 || k.sg == want_rd) && (want_rs < 0 || k.occ == want_rs)) pick.push_back(k.off);
+      if (pick.empty()) return -1;
+      const int D = sb.bdl[b], dR = sb.bdr[b];
+      const int64_t o = matrix(D, D);
+      for (int co : pick)
+        T.add_term(Operand{sb.boff[b] + co, B_X, dR}, Operand{sb.boff[b] + co, B_X, dR}, 1, 2, 1.0);
+      return o;
+    };
+    for (int b = 0; b < nb; ++b) {
+      s_rd[b] = select(b, 1, -1);
+      s_rs[b] = select(b, -1, 1);
+      s_rr[b] = select(b, 1, 1);
+    }
+    // transitions <bra| ... a_j |ket>: ket columns with orbital j occupied, bra columns of the
+    // block whose left sector gained q_j with j empty and the other occupation unchanged
+    const QN qj[2] = {q_rd, q_rs};
+    for (int j = 0; j < 2; ++j) {
+      bool need = c.chain.q[p] == qj[j];
+      for (int i = 0; i < p && !need; ++i) need = c.chain.q[i] == qj[j];
+      if (!need) continue;
+      for (int b = 0; b < nb; ++b) {
+        const int Q2 = Ll.sec.find(Ll.sec.q[sb.bL[b]] + qj[j]);
+        if (Q2 < 0) continue;
+        const int b2 = sb.psi_of_L[Q2];
+        if (b2 < 0) continue;
+        DMRG_REQUIRE(Rl.sec.q[sb.bR[b2]] == Rl.sec.q[sb.bR[b]] - qj[j], DMRG_EINVAL,
+                     "internal: transition block does not conserve the target");
+        std::vector<std::array<int, 3>> pairs;   // bra column, ket column, sign
+        for (const Col& k : cols[b]) {
+          if ((j == 0 ? k.sg : k.occ) != 1) continue;
+          for (const Col& k2 : cols[b2]) {
+            const bool match = j == 0 ? (k2.sg == 0 && k2.occ == k.occ) : (k2.sg == k.sg && k2.occ == 0);
+            if (match) pairs.push_back({k2.off, k.off, (j == 1 && k.sg == 1) ? -1 : 1});
+          }
+        }
+        if (pairs.empty()) continue;
+        const int D = sb.bdl[b], D2 = sb.bdl[b2], dR = sb.bdr[b], dR2 = sb.bdr[b2];
+        t_j[j][b] = matrix(D2, D);
+        b2_j[j][b] = b2;
+        for (auto& pr : pairs)
+          T.add_term(Operand{sb.boff[b2] + pr[0], B_X, dR2}, Operand{sb.boff[b] + pr[1], B_X, dR},
+                     1, 2, double(pr[2]));
+      }
+    }
+    if (q_rd == q_rs) {   // hop between the right dot and the last orbital, inside a block
+      for (int b = 0; b < nb; ++b) {
+        int ket = -1, bra = -1;
+        for (const Col& k : cols[b]) {
+          if (k.sg == 0 && k.occ == 1) ket = k.off;
+          if (k.sg == 1 && k.occ == 0) bra = k.off;
+        }
+        if (ket < 0 || bra < 0) continue;
+        const int D = sb.bdl[b], dR = sb.bdr[b];
+        t_rr[b] = matrix(D, D);
+        T.add_term(Operand{sb.boff[b] + bra, B_X, dR}, Operand{sb.boff[b] + ket, B_X, dR}, 1, 2,
+                   1.0);
+      }
+    }
+  }
+  // ---- rectangle dot products, grouped by slot
+  std::vector<std::vector<RectDot>> slots;
+  auto slot = [&]() {
+    slots.emplace_back();
+    return int(slots.size()) - 1;
+  };
+  auto trace = [&](int k, int64_t base, int D, int off_r, int off_c, int n, double sign) {
+    slots[k].push_back(RectDot{0, base + int64_t(off_r) * D + off_c, -1, D, n, n, sign});
+  };
+  // n_i (x) rows/cols sigma of a D x D matrix at base, summed over both pieces (sg < 0) or
+  // one piece
+  auto n_dot = [&](int k, int i, int b, int64_t base, int sg_only) {
+    const int Q = sb.bL[b], D = sb.bdl[b];
+    for (int sg = 0; sg < 2; ++sg) {
+      if (sg_only >= 0 && sg != sg_only) continue;
+      int off, len;
+      if (!mi_piece(Ll, Q, sg, &off, &len)) continue;
+      const int s_in = Ll.pblk[Q][sg];
+      const int x = B.by_in[size_t(2 * i) * nsB + s_in];
+      if (x < 0) continue;
+      DMRG_REQUIRE(B.sec.d[s_in] == len && B.blocks[x].so == s_in, DMRG_EINVAL,
+                   "internal: occupation block does not fit its piece");
+      slots[k].push_back(RectDot{B.blocks[x].off, base + int64_t(off) * D + off, len, D, len, len, 1.0});
+    }
+  };
+  const int k_np = slot();
+  std::vector<int> k_n(p), k_nn(p), k_h(p, -1);
+  for (int i = 0; i < p; ++i) {
+    k_n[i] = slot();
+    k_nn[i] = slot();
+    if (c.chain.q[i] == qp) k_h[i] = slot();
+  }
+  for (int b = 0; b < nb; ++b) {
+    const int Q = sb.bL[b], D = sb.bdl[b];
+    int o0, l0, o1, l1;
+    const bool has0 = mi_piece(Ll, Q, 0, &o0, &l0), has1 = mi_piece(Ll, Q, 1, &o1, &l1);
+    if (has1) trace(k_np, rho[b], D, o1, o1, l1, 1.0);
+    for (int i = 0; i < p; ++i) {
+      n_dot(k_n[i], i, b, rho[b], -1);
+      n_dot(k_nn[i], i, b, rho[b], 1);
+      if (k_h[i] >= 0 && has0 && has1) {
+        const int s1 = Ll.pblk[Q][1], s0 = Ll.pblk[Q][0];
+        const int x = B.by_in[size_t(2 * i + 1) * nsB + s1];
+        if (x < 0) continue;
+        DMRG_REQUIRE(B.blocks[x].so == s0 && B.sec.d[s0] == l0 && B.sec.d[s1] == l1, DMRG_EINVAL,
+                     "internal: creation block does not fit its pieces");
+        slots[k_h[i]].push_back(RectDot{B.blocks[x].off, rho[b] + int64_t(o0) * D + o1, l1, D, l0,
+                                        l1, parity(B.sec.q[s1])});
+      }
+    }
+  }
+  // last step: pairs with the right dot (j = 0) and the last orbital (j = 1)
+  int k_nj[2] = {-1, -1}, k_njj = -1, k_hjj = -1, k_pnj[2] = {-1, -1}, k_phj[2] = {-1, -1};
+  std::vector<int> k_inj[2], k_ihj[2];
+  if (last) {
+    const std::vector<int64_t>* sel[2] = {&s_rd, &s_rs};
+    const QN qj[2] = {q_rd, q_rs};
+    k_njj = slot();
+    if (q_rd == q_rs) k_hjj = slot();
+    for (int j = 0; j < 2; ++j) {
+      k_nj[j] = slot();
+      k_pnj[j] = slot();
+      if (qp == qj[j]) k_phj[j] = slot();
+      k_inj[j].assign(p, -1);
+      k_ihj[j].assign(p, -1);
+      for (int i = 0; i < p; ++i) {
+        k_inj[j][i] = slot();
+        if (c.chain.q[i] == qj[j]) k_ihj[j][i] = slot();
+      }
+    }
+    for (int b = 0; b < nb; ++b) {
+      const int Q = sb.bL[b], D = sb.bdl[b];
+      if (s_rr[b] >= 0) trace(k_njj, s_rr[b], D, 0, 0, D, 1.0);
+      if (t_rr[b] >= 0) trace(k_hjj, t_rr[b], D, 0, 0, D, 1.0);
+      for (int j = 0; j < 2; ++j) {
+        const int64_t S = (*sel[j])[b];
+        if (S >= 0) {
+          trace(k_nj[j], S, D, 0, 0, D, 1.0);
+          int o1, l1;
+          if (mi_piece(Ll, Q, 1, &o1, &l1)) trace(k_pnj[j], S, D, o1, o1, l1, 1.0);
+          for (int i = 0; i < p; ++i) n_dot(k_inj[j][i], i, b, S, -1);
+        }
+        const int64_t Tt = t_j[j][b];
+        if (Tt < 0) continue;
+        const int b2 = b2_j[j][b], Q2 = sb.bL[b2];
+        // c+_p c_j: the left dot empty in the ket, occupied in the bra, block state unchanged
+        int o0, l0, o1b, l1b;
+        if (k_phj[j] >= 0 && mi_piece(Ll, Q, 0, &o0, &l0) && mi_piece(Ll, Q2, 1, &o1b, &l1b)) {
+          DMRG_REQUIRE(Ll.pblk[Q][0] == Ll.pblk[Q2][1] && l0 == l1b, DMRG_EINVAL,
+                       "internal: left-dot transition pieces differ");
+          trace(k_phj[j], Tt, D, o1b, o0, l0, 1.0);
+        }
+        // c+_i c_j, i in the block: the piece of the left dot unchanged
+        for (int i = 0; i < p; ++i) {
+          if (k_ihj[j][i] < 0) continue;
+          for (int sg = 0; sg < 2; ++sg) {
+            int oi, li, oo, lo;
+            if (!mi_piece(Ll, Q, sg, &oi, &li) || !mi_piece(Ll, Q2, sg, &oo, &lo)) continue;
+            const int s_in = Ll.pblk[Q][sg], s_out = Ll.pblk[Q2][sg];
+            const int x = B.by_in[size_t(2 * i + 1) * nsB + s_in];
+            if (x < 0) continue;
+            DMRG_REQUIRE(B.blocks[x].so == s_out && B.sec.d[s_in] == li && B.sec.d[s_out] == lo,
+                         DMRG_EINVAL, "internal: creation block does not fit its pieces");
+            const double sign = parity(B.sec.q[s_in]) * (sg ? -1.0 : 1.0);
+            slots[k_ihj[j][i]].push_back(
+                RectDot{B.blocks[x].off, Tt + int64_t(oo) * D + oi, li, D, lo, li, sign});
+          }
+        }
+      }
+    }
+  }
+  // ---- device work: the matrices, the rectangles, the sums per slot
+  int64_t be[NBASE] = {0};
+  be[B_X] = sb.size;
+  be[B_Y] = std::max<int64_t>(roff, 1);
+  DevTaskList L;
+  L.build(T, be, c.stream);
+  DevBuf<double> R;
+  R.alloc(std::max<int64_t>(roff, 1));
+  Bases<double> bb{};
+  bb.p[B_X] = c.psi.p;
+  bb.p[B_Y] = R.p;
+  run_gemm_tasks<double>(L, bb, 1, c.stream);
+  std::vector<RectDot> flat;
+  std::vector<int64_t> ptr(1, 0);
+  for (auto& v : slots) {
+    for (const RectDot& t : v) mi_check(t, B.n_elems, roff);
+    flat.insert(flat.end(), v.begin(), v.end());
+    ptr.push_back(int64_t(flat.size()));
+  }
+  const int64_t ns = int64_t(slots.size());
+  DevBuf<RectDot> dt;
+  DevBuf<int64_t> dp;
+  DevBuf<double> part, out;
+  dt.upload(flat, c.stream);
+  dp.upload(ptr, c.stream);
+  part.alloc(std::max<int64_t>(int64_t(flat.size()), 1));
+  out.alloc(std::max<int64_t>(ns, 1));
+  rect_dots(dt.p, int64_t(flat.size()), B.data.p, R.p, part.p, c.stream);
+  slot_sums(dp.p, ns, part.p, out.p, c.stream);
+  std::vector<double> h(size_t(std::max<int64_t>(ns, 1)));
+  DMRG_CUDA(cudaMemcpyAsync(h.data(), out.p, sizeof(double) * ns, cudaMemcpyDeviceToHost,
+                            c.stream));
+  sync(c);
+  // ---- two-orbital density matrices of this step's pairs
+  auto val = [&](int k) { return k >= 0 ? h[k] : 0.0; };
+  auto put = [&](int i, int j, double ni, double nj, double nij, double hij) {
+    double si, sj, I;
+    mi_pair(ni, nj, nij, hij, &si, &sj, &I);
+    mr.I[size_t(i) * N + j] = mr.I[size_t(j) * N + i] = I;
+    if (last) {
+      mr.s[i] = si;
+      mr.s[j] = sj;
+    }
+  };
+  const double np_ = h[k_np];
+  for (int i = 0; i < p; ++i) put(i, p, h[k_n[i]], np_, h[k_nn[i]], val(k_h[i]));
+  if (last) {
+    const int jpos[2] = {N - 2, N - 1};
+    for (int j = 0; j < 2; ++j) {
+      const double nj = h[k_nj[j]];
+      for (int i = 0; i < p; ++i) put(i, jpos[j], h[k_n[i]], nj, h[k_inj[j][i]], val(k_ihj[j][i]));
+      put(p, jpos[j], np_, nj, h[k_pnj[j]], val(k_phj[j]));
+    }
+    put(N - 2, N - 1, h[k_nj[0]], h[k_nj[1]], h[k_njj], val(k_hjj));
+  }
+}
+
+// after the truncation at p: the carried operators and those of orbital p, embedded in the
+// enlarged left space (block operator (x) 1 of the site; n_p and c+_p = parity of the block
+// (x) c+ of the site), renormalized with the new block's basis
+static void mi_carry(Ctx& c, MiRun& mr, Super& sb, int p) {
+  const Layout& Ll = sb.Ll;
+  const OpSet& B = mr.ops;
+  const int nsB = B.sec.size();
+  const Iso& iso = c.left[p].iso;
+  DMRG_REQUIRE(iso.lay.sec.q == Ll.sec.q && iso.lay.sec.d == Ll.sec.d, DMRG_EINVAL,
+               "internal: the new basis does not refer to the enlarged space");
+  OpSet E;
+  E.sec = Ll.sec;
+  E.nlab = 2 * (p + 1);
+  E.lab_ptr.assign(size_t(E.nlab) + 1, 0);
+  std::vector<EmbedTask> emb;
+  int64_t eoff = 0;
+  const int nE = Ll.sec.size();
+  for (int lab = 0; lab < E.nlab; ++lab) {
+    E.lab_ptr[lab] = int64_t(E.blocks.size());
+    const int i = lab / 2;
+    const bool cre = lab & 1;
+    for (int Q = 0; Q < nE; ++Q) {
+      const int Q2 = cre ? Ll.sec.find(Ll.sec.q[Q] + c.chain.q[i]) : Q;
+      if (Q2 < 0) continue;
+      const int Din = Ll.sec.d[Q], Dout = Ll.sec.d[Q2];
+      std::vector<EmbedTask> here;
+      if (i < p) {
+        for (int sg = 0; sg < 2; ++sg) {
+          int oi, li, oo, lo;
+          if (!mi_piece(Ll, Q, sg, &oi, &li) || !mi_piece(Ll, Q2, sg, &oo, &lo)) continue;
+          const int s_in = Ll.pblk[Q][sg], s_out = Ll.pblk[Q2][sg];
+          const int x = B.by_in[size_t(lab) * nsB + s_in];
+          if (x < 0) continue;
+          DMRG_REQUIRE(B.blocks[x].so == s_out && B.sec.d[s_in] == li && B.sec.d[s_out] == lo,
+                       DMRG_EINVAL, "internal: carried block does not fit its pieces");
+          here.push_back(EmbedTask{B.blocks[x].off, int64_t(oo) * Din + oi, li, Din, lo, li, 1.0});
+        }
+      } else if (!cre) {
+        int o1, l1;
+        if (mi_piece(Ll, Q, 1, &o1, &l1))
+          here.push_back(EmbedTask{-1, int64_t(o1) * Din + o1, 0, Din, l1, l1, 1.0});
+      } else {
+        int o0, l0, o1, l1;
+        if (mi_piece(Ll, Q, 0, &o0, &l0) && mi_piece(Ll, Q2, 1, &o1, &l1)) {
+          DMRG_REQUIRE(Ll.pblk[Q][0] == Ll.pblk[Q2][1] && l0 == l1, DMRG_EINVAL,
+                       "internal: creation pieces differ");
+          const QN qb = B.sec.q[Ll.pblk[Q][0]];
+          here.push_back(EmbedTask{-1, int64_t(o1) * Din + o0, 0, Din, l1, l0,
+                                   ((qb.a + qb.b) & 1) ? -1.0 : 1.0});
+        }
+      }
+      if (here.empty()) continue;
+      for (EmbedTask& t : here) {
+        DMRG_REQUIRE(t.nc <= t.ldd && t.dst + int64_t(t.nr - 1) * t.ldd + t.nc <= int64_t(Dout) * Din &&
+                         (t.src < 0 || t.src + int64_t(t.nr - 1) * t.lds + t.nc <= B.n_elems),
+                     DMRG_EINVAL, "internal: embedded block out of range");
+        t.dst += eoff;
+        emb.push_back(t);
+      }
+      E.blocks.push_back(OpBlock{Q2, Q, eoff});
+      eoff += int64_t(Dout) * Din;
+    }
+  }
+  E.lab_ptr[E.nlab] = int64_t(E.blocks.size());
+  E.n_elems = eoff;
+  E.data.alloc(std::max<int64_t>(eoff, 1));
+  DMRG_CUDA(cudaMemsetAsync(E.data.p, 0, sizeof(double) * std::max<int64_t>(eoff, 1), c.stream));
+  DevBuf<EmbedTask> de;
+  de.upload(emb, c.stream);
+  embed_blocks(de.p, int64_t(emb.size()), B.data.p, E.data.p, c.stream);
+  E.index_by_in();
+  OpSet out;
+  project(c, E, iso, out);
+  sync(c);
+  mr.ops = std::move(out);
+}
+
 static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st,
-                 double* late_energy = nullptr) {
+                 double* late_energy = nullptr, MiRun* mi = nullptr) {
   double t0 = now_s();
   Super& sb = super_at(c, p);
   // the block that the next step of this sweep enlarges on the side this step leaves as
@@ -2515,7 +2963,9 @@ static void step(Ctx& c, int p, int dir, int M, dmrg_step_stats* st,
   const double flops = sb.flops, bytes = sb.bytes;
   c.psi_valid = true;
   c.psi_p = p;
+  if (mi) mi_measure(c, *mi, sb, p);
   TruncResult tr = truncate_renormalize(c, p, dir, M);   // overlaps the Rayleigh quotient
+  if (mi) mi_carry(c, *mi, sb, p);
   const bool late = late_energy && c.rq_pending;
   if (!late) dav_energy(c, r);
   if (st) {
@@ -2622,6 +3072,7 @@ extern "C" int dmrg_create(const dmrg_problem* prob, const dmrg_options* opt, dm
       (void)cudaGetLastError();
     }
     build_chain(prob, c->chain);
+    c->order.assign(prob->order, prob->order + c->chain.N);
     build_mpo(c->chain, c->mpo);
     c->N = c->chain.N;
     build_reach(*c);
@@ -2931,6 +3382,30 @@ extern "C" int dmrg_sweep(dmrg_ctx* c, int32_t M, dmrg_step_stats* steps, double
     }
     if (steps) std::copy(all.begin(), all.end(), steps);
     if (energy && !all.empty()) *energy = all.back().energy;
+  });
+}
+
+extern "C" int dmrg_mutual_information(dmrg_ctx* c, int32_t M, double* I, double* s,
+                                       dmrg_step_stats* steps) {
+  return guarded(c, [&] {
+    DMRG_REQUIRE(c->built, DMRG_EINVAL, "dmrg_build_blocks has not been called");
+    DMRG_REQUIRE(I != nullptr && s != nullptr, DMRG_EINVAL, "NULL output");
+    DMRG_REQUIRE(M >= 1, DMRG_EINVAL, "M must be positive");
+    DMRG_REQUIRE(c->n_roots == 1, DMRG_EINVAL, "the mutual information is for one targeted state");
+    const int N = c->N;
+    MiRun mr;
+    mr.N = N;
+    mr.I.assign(size_t(N) * N, 0.0);
+    mr.s.assign(size_t(N), 0.0);
+    mi_init(*c, mr);
+    std::vector<dmrg_step_stats> all(size_t(N - 3));
+    for (int p = 1; p <= N - 3; ++p) step(*c, p, 0, M, &all[p - 1], nullptr, &mr);
+    settle_energy(*c);
+    if (steps) std::copy(all.begin(), all.end(), steps);
+    for (int i = 0; i < N; ++i) {
+      s[c->order[i]] = mr.s[i];
+      for (int j = 0; j < N; ++j) I[size_t(c->order[i]) * N + c->order[j]] = mr.I[size_t(i) * N + j];
+    }
   });
 }
 
