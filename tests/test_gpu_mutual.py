@@ -87,10 +87,14 @@ def test_mutual_information_equals_the_written_out_states(P, space, Np, Nn, tM, 
     assert I.max() > 1e-3
 
 
-def test_mutual_information_at_complete_bases_is_exact(P):
+@pytest.mark.parametrize("seed", [3, 1])
+def test_mutual_information_at_complete_bases_is_exact(P, seed):
+    """Seed 3: a J >= 1 ground state (its M = 0 member); seed 1: a J = 0 ground state, whose
+    one-orbital entropies are equal over the m-substates of each j-shell (the paper's
+    observation for the J = 0 states)."""
     from oracle.entropy import mutual_information_dets
     from oracle.hamiltonian import ed_sector
-    prob = _problem("p", 2, 2, 0, 3, True)
+    prob = _problem("p", 2, 2, 0, seed, True)
     basis, H = ed_sector(prob, 2, 2, 0)
     w, V = np.linalg.eigh(H)
     I_ex, s_ex = mutual_information_dets(np.array(basis, dtype=np.uint64), V[:, 0],
@@ -103,6 +107,13 @@ def test_mutual_information_at_complete_bases_is_exact(P):
     assert abs(steps[-1]["energy"] - w[0]) <= 1e-9
     assert np.max(np.abs(I - I_ex)) <= 1e-8
     assert np.max(np.abs(s - s_ex)) <= 1e-8
+    if seed == 1:
+        _, H2 = ed_sector(prob, 2, 2, 2)
+        assert np.linalg.eigvalsh(H2)[0] > w[0] + 1.0      # no M = 1 state at E0: J = 0
+        for sp in (0, 1):
+            for orb in set(int(x) for x in prob.orbital):
+                sel = (np.asarray(prob.species) == sp) & (np.asarray(prob.orbital) == orb)
+                assert np.ptp(s[sel]) <= 1e-8, (sp, orb, s[sel])
 
 
 def test_mutual_information_arguments(P):
