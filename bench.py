@@ -328,8 +328,10 @@ def run_next_rows(P, prob, init, M, e_fixed):
     """Rows beyond the core path, each timed once by wall clock around a whole sweep:
     dynamic block state selection on the default workload (mixed path, M_min = 256,
     ceiling M, discarded-weight target 1e-5; compared with the fixed-M sweep from the same
-    starting state), and two-state targeting on pf 4p+4n at M = 1024 in FP64 (one state
-    vs the two lowest, from the same starting state)."""
+    starting state), two-state targeting on pf 4p+4n at M = 1024 in FP64 (one state vs the
+    two lowest, from the same starting state), and the all-pairs mutual information of
+    pf 4p+4n at M = 256 with the Fiedler order computed from it."""
+    import numpy as np
     import torch
     from gen import make_problem, initial_mps
     out = {}
@@ -378,6 +380,32 @@ def run_next_rows(P, prob, init, M, e_fixed):
                             "E0_one_state": s1[-1]["energy"]}
     except Exception as exc:
         out["two_state"] = {"error": str(exc)}
+    try:
+        # the ordering analysis on the device: pf 4p+4n in its natural order, two sweeps at
+        # M = 256, then the all-pairs mutual information from a half sweep and the Fiedler
+        # order of that matrix
+        prob3 = make_problem("pf", 4, 4, 0, seed=2)
+        d = P.DMRG(prob3, precision=P.FP64, dav_tol=1e-8)
+        d.build_blocks(initial_mps(prob3, 256, 2002))
+        d.sweep(256)
+        d.sweep(256)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        I, s_i, steps = d.mutual_information(256)
+        t_mi = time.perf_counter() - t0
+        d.close()
+        order, _ = P.fiedler_order(I)
+        iu = np.triu_indices(I.shape[0], 1)
+        top = np.argsort(I[iu])[::-1][:5]
+        out["mutual_information"] = {
+            "workload": "pf 4p+4n seed 2, natural order, two FP64 sweeps at M=256, then the "
+                        "half sweep of dmrg_mutual_information at M=256",
+            "half_sweep_s": t_mi, "energy": steps[-1]["energy"],
+            "I_max": float(I.max()), "s_max": float(s_i.max()),
+            "top_pairs": [[int(iu[0][k]), int(iu[1][k]), float(I[iu][k])] for k in top],
+            "fiedler_order": [int(x) for x in order]}
+    except Exception as exc:
+        out["mutual_information"] = {"error": str(exc)}
     return out
 
 
