@@ -206,16 +206,27 @@ def run_reference(args):
     return 0
 
 
-def _cpu_baseline_subprocess(steps, warmup):
-    """The oracle sample in a child process pinned to one BLAS thread."""
+def _cpu_baseline_start(steps, warmup):
+    """Starts the oracle sample in a child process pinned to one BLAS thread (one of the
+    host's cores, beside the GPU work, which the device timers measure)."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "print(json.dumps(bench.cpu_oracle_sample(%d, %d)))" % (ROOT, steps, warmup))
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                       timeout=900)
-    if r.returncode != 0:
+    return subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True)
+
+
+def _cpu_baseline_finish(proc):
+    """The child's result as the cpu_baseline object (None if it failed)."""
+    try:
+        out, _ = proc.communicate(timeout=900)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        proc.communicate()
         return None
-    tf, secs, nprod, desc = json.loads(r.stdout.strip().splitlines()[-1])
+    if proc.returncode != 0 or not out.strip():
+        return None
+    tf, secs, nprod, desc = json.loads(out.strip().splitlines()[-1])
     return {"value": tf, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": desc,
             "host_cores": os.cpu_count()}
 
@@ -537,6 +548,10 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
+    # the oracle's CPU sample runs in a child process on one host core while the GPU works
+    cpu_proc = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu_proc = _cpu_baseline_start(args.steps, args.warmup)
     torch.cuda.set_device(local)
     from paper_1507_00161_gb300.build import build
     if rank == 0:
@@ -716,9 +731,7 @@ def run_gpu(args):
         if dist:
             dist.destroy_process_group()
         return 0
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cpu = _cpu_baseline_subprocess(args.steps, args.warmup)
+    cpu = _cpu_baseline_finish(cpu_proc) if cpu_proc is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": len(timed), "warmup": len(warm), "ms_per_step": 1e3 * total_s / len(timed),
