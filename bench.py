@@ -213,7 +213,7 @@ def _cpu_baseline_start(steps, warmup):
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "print(json.dumps(bench.cpu_oracle_sample(%d, %d)))" % (ROOT, steps, warmup))
     return subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
-                            stderr=subprocess.PIPE, text=True)
+                            stderr=subprocess.DEVNULL, text=True)
 
 
 def _cpu_baseline_finish(proc):
