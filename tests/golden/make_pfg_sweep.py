@@ -22,7 +22,8 @@ OUT = os.path.join(HERE, "pfg_2p2n_M4.json")
 SPACE, NP, NN, TM, SEED, M, MPS_SEED = "pfg", 2, 2, 4, 5, 16, 5005
 
 
-def main():
+def compute():
+    """The stored record (a dict), computed from oracle/ and gen/."""
     t0 = time.time()
     prob = make_problem(SPACE, NP, NN, TM, seed=SEED)
     o = OracleDMRG(prob, initial_mps(prob, M, MPS_SEED))
@@ -34,9 +35,14 @@ def main():
     out = {"workload": "pf+g9/2 shell, 60 m-scheme sites, 2p+2n, 2M_z=4, seed %d" % SEED,
            "generator": "gen.make_problem('%s', %d, %d, %d, seed=%d)" % (SPACE, NP, NN, TM, SEED),
            "M": M, "mps_seed": MPS_SEED, "steps": steps, "seconds": time.time() - t0}
+    return out
+
+
+def main():
+    out = compute()
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1)
-    print("wrote", OUT, steps[-1]["energy"], time.time() - t0)
+    print("wrote", OUT, out["steps"][-1]["energy"], out["seconds"])
 
 
 if __name__ == "__main__":
