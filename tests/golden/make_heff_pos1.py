@@ -28,7 +28,8 @@ from oracle.dmrg import OracleDMRG             # noqa: E402
 CASES = {"pf4p4n": ("pf", 4, 4, 0, 2, 1024, 2002), "pf8p8n": ("pf", 8, 8, 0, 3, 4096, 3003)}
 
 
-def main(name):
+def compute(name):
+    """The stored record of one case (a dict), computed from oracle/ and gen/."""
     space, Np, Nn, tM, seed, M0, mseed = CASES[name]
     t0 = time.time()
     prob = make_problem(space, Np, Nn, tM, seed=seed)
@@ -52,9 +53,14 @@ def main(name):
                         for j in range(4)],
         "seconds": {"setup": t1 - t0, "product": t2 - t1},
     }
+    return out
+
+
+def main(name):
+    out = compute(name)
     with open(os.path.join(HERE, "heff_pos1_%s.json" % name), "w") as f:
         json.dump(out, f)
-    print(name, out["seconds"], size)
+    print(name, out["seconds"], out["size"])
 
 
 if __name__ == "__main__":
